@@ -1,0 +1,420 @@
+"""Benchmark: multi-key bootstrapped gates per second on one GB300.
+
+Workload (full-size, 2 parties): n = 560, N = 1024, gadget base 2^8 with
+d = 3, key-switching base 2^2 with t = 8, LWE sigma 2^-15; 4096 independent
+gates per step, gate type and input bits uniform (seeded); c1 encrypted by
+party 0 and c2 by party 1, so every CMux step of the blind rotation is active.
+One step = the whole hot path over the batch: linear part, modulus switch,
+blind rotation (exact NTT form), SampleExtract, key switch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain schoolbook implementation)
+on the host cores over a bounded sample of the same workload.  Under torchrun
+every rank runs its own 4096-gate batch on its own GPU (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MK bootstrapped gates/sec (2 and 4 parties, N=1024); p50/p99 gate latency"
+UNIT = "gates/s"
+WORKLOAD = "full-size MK gate bootstrap, k=2 parties, n=560, N=1024, 4096 random gates per step"
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard_seed(config_id, rank):
+    """Each rank draws its own batch of gates (independent units, weak scaling)."""
+    return config_id * 100 + rank
+
+
+def reduce_max(value, world):
+    """Max over ranks (time of the slowest rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            return None
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline bookkeeping
+def modmuls_per_cmux(P):
+    """64-bit modular multiplies of one CMux step of the NTT form: (k+2)(d+1)
+    length-N transforms of (N/2) log2 N butterflies, plus (2k+4) d N pointwise
+    products (hybrid product, phase A and B)."""
+    k, d, N = P["k"], P["d"], P["N"]
+    logn = N.bit_length() - 1
+    return (k + 2) * (d + 1) * (N // 2) * logn + (2 * k + 4) * d * N
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mk_bootstrap.cuh", "mk_br_1024.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2205_05825_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_gate():
+    """DRAM bytes per gate of the blind-rotation kernel from the committed ncu
+    summary, or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "bootstrap_ntt_k2_n1024_traffic.txt")
+    try:
+        kv = dict(line.split(":", 1) for line in open(path) if ":" in line)
+    except OSError:
+        return None
+    if kv.get("kernel_source_sha256_16", "").strip() != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_gate"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+    B.load(build_if_missing=True)
+
+    def setup(k, G):
+        P = W.full_params(k)
+        ctx = B.Context(P, W.CRS_SEED, device=dev_index)
+        for i, s in enumerate(W.party_seeds(k)):
+            ctx.keygen(i, s)
+        cfg = shard_seed(2, rank)
+        types, b1, b2 = W.random_gates(G, config_id=cfg)
+        c1 = ctx.encrypt(0, b1, W.encryption_seed(cfg, 0))
+        c2 = ctx.encrypt(1, b2, W.encryption_seed(cfg, 1))
+        truth = np.array([[a & b, a | b, 1 - (a & b), 1 - (a | b), a ^ b, 1 - (a ^ b)][t]
+                          for t, a, b in zip(types, b1.astype(int), b2.astype(int))], np.uint8)
+        return P, ctx, types, c1, c2, truth
+
+    G = args.gates
+    P, ctx, types, c1, c2, truth = setup(2, G)
+    tdev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32
+                                      else np.ascontiguousarray(a)).cuda()
+    d_types, d_c1, d_c2 = tdev(types.astype(np.uint8)), tdev(c1), tdev(c2)
+    d_out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # autotune the blind-rotation variant on a sample of random ciphertexts
+    variant, variant_ms = ctx.autotune(min(args.autotune_gates, G))
+
+    # warm-up (also uploads the keys)
+    for _ in range(args.warmup):
+        ctx.gates(d_types, d_c1, d_c2, d_out)
+    torch.cuda.synchronize()
+    ok = np.array_equal(ctx.decrypt(d_out), truth)
+
+    # timed region: exactly K steps, barrier + sync on both sides
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    ctx.timing_enable(True)
+    ctx.timing_reset()
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        step_ev[s][0].record(stream)
+        ctx.gates(d_types, d_c1, d_c2, d_out)
+        step_ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    br_ms, br_n = ctx.timing_read(0)
+    ks_ms, ks_n = ctx.timing_read(1)
+    ctx.timing_enable(False)
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    total_ms_max = reduce_max(total_ms, world)
+    value = G * args.steps * world / (total_ms_max * 1e-3)
+    launches_per_step = 3 * ((G + 4095) // 4096)
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    h_types = torch.from_numpy(types.astype(np.uint8)).pin_memory()
+    h_c1 = torch.from_numpy(c1.view(np.int32)).pin_memory()
+    h_c2 = torch.from_numpy(c2.view(np.int32)).pin_memory()
+    h_out = torch.empty((G, ctx.W), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_types.copy_(h_types, non_blocking=True)
+        d_c1.copy_(h_c1, non_blocking=True)
+        d_c2.copy_(h_c2, non_blocking=True)
+        ctx.gates(d_types, d_c1, d_c2, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), world)
+    e2e_value = G * e2e_steps * world / (e2e_ms * 1e-3)
+    ok = ok and np.array_equal(ctx.decrypt(h_out.numpy().view(np.uint32)), truth)
+
+    # one-gate-per-launch form (the plain denominator), a few gates
+    plain_g = args.plain_gates
+    ctx.set_batch(1)
+    ctx.gates(d_types[:1], d_c1[:1], d_c2[:1], d_out[:1])
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    ctx.gates(d_types[:plain_g].contiguous(), d_c1[:plain_g].contiguous(), d_c2[:plain_g].contiguous(),
+              d_out[:plain_g])
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    plain_rate = plain_g / (plain_ms * 1e-3)
+    ctx.set_batch(4096)
+
+    # k = 4 parties (second half of the metric): one timed batch
+    k4 = None
+    if args.k4_gates > 0:
+        P4, ctx4, t4, a4, b4, tr4 = setup(4, args.k4_gates)
+        ctx4.autotune(min(args.autotune_gates, args.k4_gates))
+        dt4, da4, db4 = tdev(t4.astype(np.uint8)), tdev(a4), tdev(b4)
+        do4 = torch.zeros((args.k4_gates, ctx4.W), dtype=torch.int32, device="cuda")
+        ctx4.gates(dt4, da4, db4, do4)
+        torch.cuda.synchronize()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        ctx4.gates(dt4, da4, db4, do4)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        k4_ms = q0.elapsed_time(q1)
+        k4_ok = bool(np.array_equal(ctx4.decrypt(do4), tr4))
+        k4 = {"gates_per_s": args.k4_gates / (k4_ms * 1e-3), "gates": args.k4_gates, "ms_per_batch": k4_ms,
+              "decrypt_ok": k4_ok, "active_cmux_steps_per_gate": 2 * P4["n"]}
+        ctx4.close()
+
+    # roofline of the dominant kernel (blind rotation), live from the timed region
+    avg_br_ms = br_ms / max(br_n, 1)
+    mm_per_gate = modmuls_per_cmux(P) * P["k"] * P["n"]
+    achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / 1e9  # G modmul/s
+    peak = B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048) / 1e9
+    traffic_pg = ncu_traffic_per_gate()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G modmul/s",
+                "frac": achieved / peak, "traffic": (traffic_pg * G if traffic_pg is not None else None),
+                "kernel": "bootstrap_ntt_kernel<10, variant %d>" % variant, "algorithmic_modmuls_per_gate": mm_per_gate,
+                "peak_source": "measured: register-resident Goldilocks butterfly loop on every SM "
+                               "(mk_measure_butterfly_rate), one modmul per butterfly",
+                "br_share_of_step": br_ms / total_ms if total_ms else None}
+
+    ctx.close()
+    if rank != 0:
+        return
+    sm = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parties": 2, "gates_per_step": G, "n": P["n"], "N": P["N"],
+                   "bg_bit": P["bg_bit"], "d": P["d"], "ks_bit": P["ks_bit"], "t": P["t"],
+                   "sigma_lwe": P["sigma_lwe"], "sigma_rlwe": P["sigma_rlwe"], "form": "ntt64 (exact)",
+                   "variant": variant, "autotune_ms": variant_ms,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "no flush: per-step working set (BK 82 MB NTT domain + KS 110 MB + 37 MB "
+                         "ciphertexts) exceeds the 129 MB L2"},
+        "latency_ms": {"p50": float(np.percentile(sm, 50)), "p99": float(np.percentile(sm, 99)),
+                       "note": "every gate of a batched launch completes with its batch"},
+        "plain_one_gate_per_launch": {"gates_per_s": plain_rate, "gates": plain_g,
+                                      "latency_ms": plain_ms / plain_g,
+                                      "batched_over_plain": value / world / plain_rate},
+        "k4": k4,
+        "decrypt_ok": bool(ok),
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(G + 2 * G * ctx.W * 4),
+                "d2h_bytes_per_step": int(G * ctx.W * 4), "steps": e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline,
+        "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def _oracle_setup():
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.full_params(2)
+    return o, W, P, o.keygen(P, W.CRS_SEED, W.party_seeds(2))
+
+
+def _oracle_step(o, W, P, keys, sample, cores):
+    types, b1, b2 = W.random_gates(sample, config_id=shard_seed(2, 0))
+    c1 = o.encrypt(P, keys, 0, b1, W.encryption_seed(2, 0))
+    c2 = o.encrypt(P, keys, 1, b2, W.encryption_seed(2, 1))
+    t0 = time.perf_counter()
+    out = o.gates(P, keys, types, c1, c2, nthreads=cores)
+    dt = time.perf_counter() - t0
+    truth = np.array([[a & b, a | b, 1 - (a & b), 1 - (a | b), a ^ b, 1 - (a ^ b)][t]
+                      for t, a, b in zip(types, b1.astype(int), b2.astype(int))], np.uint8)
+    return dt, bool(np.array_equal(o.decrypt(P, keys, out), truth))
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, OpenMP across gates on the host cores, over a
+    bounded sample of the workload (gates/s extrapolated from the sample)."""
+    o, W, P, keys = _oracle_setup()
+    cores = o.default_threads()
+    sample = max(cores, args.cpu_sample)
+    dt, ok = _oracle_step(o, W, P, keys, sample, cores)
+    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d gates of the same workload (k=2, n=560, N=1024), schoolbook products, "
+                      "OpenMP across gates, %.1f s" % (sample, dt), "decrypt_ok": ok}
+
+
+def run_reference(args):
+    """Reference arm: the oracle timed on the host cores; each step is a bounded
+    sample (one gate per core) of the 4096-gate workload."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    o, W, P, keys = _oracle_setup()
+    cores = o.default_threads()
+    sample = cores
+    for _ in range(args.warmup):
+        _oracle_step(o, W, P, keys, 1, 1)
+    times, oks = [], []
+    for _ in range(args.steps):
+        dt, ok = _oracle_step(o, W, P, keys, sample, cores)
+        times.append(dt)
+        oks.append(ok)
+    value = sample * len(times) / sum(times)
+    desc = ("%d gates per step (one per core) of the same workload (k=2, n=560, N=1024), schoolbook "
+            "products, OpenMP across gates" % sample)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parties": 2, "n": 560, "N": 1024, "form": "schoolbook (oracle)",
+                       "gates_per_step": sample},
+            "impl": "reference", "decrypt_ok": all(oks),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--gates", type=int, default=4096)
+    ap.add_argument("--plain-gates", type=int, default=4)
+    ap.add_argument("--k4-gates", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=16)
+    ap.add_argument("--autotune-gates", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * mk_tfhe.h -- C ABI of the GB300 multi-key TFHE gate-bootstrapping library.
+ *
+ * The calls follow the paper's statement of the problem (Jiang et al.,
+ * "Privacy-Preserving Distributed Machine Learning Made Faster",
+ * arXiv 2205.05825): MKTFHE.Setup / KeyGen / SymEnc / SymDec (Sec. 2.2),
+ * the bootstrapped gates of Sec. 3.1 (Eq. 6-11 and the NAND of Sec. 2.2),
+ * MKNOT (Eq. 8) and the k-bit two's-complement operators of Sec. 3.3-3.5
+ * (Algorithms 3-6).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Torus elements are uint32 (x stands for x / 2^32).
+ *  - A multi-key LWE ciphertext is one row uint32[k*n + 1] laid out as
+ *    (a_1 | a_2 | ... | a_k | b): party blocks of n words, then b.  Its phase
+ *    is b + sum_i <a_i, s_i>; a bit m is encoded as m/4 (Sec. 2.2, SymEnc).
+ *  - Batches are row-major [count][k*n + 1].  k-bit integers are LSB-first
+ *    rows of bit ciphertexts, two's complement: [pairs][kbits][k*n + 1].
+ *  - Pointers named d_* are device pointers on the context's device, owned by
+ *    the caller, 16-byte aligned.  Pointers named h_* are host pointers owned
+ *    by the caller.  The library owns the keys and its scratch space.
+ *  - Device work is enqueued on the context's stream and returns without
+ *    waiting, except where a call says it synchronises.  A context is not
+ *    thread-safe: one host thread per context at a time.
+ *  - Every call returns MK_OK (0) or a negative error code; mk_last_error()
+ *    gives a message for the last failure on that context.  Errors never
+ *    leave the device in a faulted state: arguments are checked on the host
+ *    before any launch.
+ */
+#ifndef MK_TFHE_H
+#define MK_TFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define MK_OK 0
+#define MK_EINVAL (-1)   /* bad argument (null pointer, size, party index) */
+#define MK_ENOMEM (-2)   /* host or device allocation failed */
+#define MK_EPARAMS (-3)  /* parameter set not supported */
+#define MK_ETIMEOUT (-4) /* a device-side wait gave up (watchdog) */
+#define MK_EDEVICE (-5)  /* CUDA error, or a device call on a host-only context */
+#define MK_ESTATE (-6)   /* keys missing for the requested operation */
+#define MK_EFORMAT (-7)  /* key blob has a bad header, size or checksum */
+
+/* ---------------------------------------------------------------- params */
+/* mkparams (Sec. 2.1, Table 7): LWE dimension n, ring dimension N, party
+ * count k, bootstrapping gadget base B = 2^bg_bit of length d, key-switching
+ * base B' = 2^ks_bit of length t (Table 7's d'), and the Gaussian noise
+ * standard deviations (torus units) of LWE and RLWE samples. */
+typedef struct mk_params {
+    uint32_t n, N, k, bg_bit, d, ks_bit, t, reserved;
+    double sigma_lwe, sigma_rlwe;
+} mk_params;
+
+enum {
+    MK_PRESET_TOY = 0,   /* n=64,  N=256,  B=2^8, d=3, B'=4, t=8, sigma 2^-25 / 2^-25 */
+    MK_PRESET_FULL = 1,  /* n=560, N=1024, B=2^8, d=3, B'=4, t=8, sigma 2^-15 / per k */
+    MK_PRESET_PAPER = 2  /* Table 7 verbatim: B=2^9, alpha=3.05e-5, beta=3.72e-9 */
+};
+
+/* Fill *out with a preset for k parties.  FULL's RLWE sigma depends on k:
+ * 2^-28 (k=1), 2^-30 (k=2,3), 2^-32 (k>=4) -- the stated 2^-25 exceeds the
+ * decision margin of the bootstrap at N=1024.  Returns MK_EINVAL for an
+ * unknown preset or k == 0. */
+int mk_params_preset(int preset, uint32_t k, mk_params *out);
+
+/* ---------------------------------------------------------------- context */
+typedef struct mk_ctx mk_ctx;
+
+/* MKTFHE.Setup (Sec. 2.2): create a context for `params`, derive the common
+ * reference string a in T_N[X]^d from crs_seed, bind CUDA device `device`
+ * and stream `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * device = -1 makes a host-only context: key generation, encryption,
+ * decryption and key export work, device calls return MK_EDEVICE.
+ * Supported: N in {256, 1024}, d*bg_bit <= 32, ks_bit*t <= 31,
+ * 1 <= k <= 8.  The context is released with mk_ctx_destroy. */
+int mk_ctx_create(const mk_params *params, uint64_t crs_seed, int device, void *stream, mk_ctx **out);
+int mk_ctx_destroy(mk_ctx *ctx);
+int mk_ctx_set_stream(mk_ctx *ctx, void *stream);
+int mk_ctx_get_params(const mk_ctx *ctx, mk_params *out);
+
+/* Negacyclic-product form used by the blind rotation. */
+enum {
+    MK_FORM_NTT = 0 /* exact: NTT over the prime 2^64 - 2^32 + 1 (bit-exact) */
+};
+int mk_ctx_set_form(mk_ctx *ctx, int form);
+
+/* Largest number of gates bootstrapped by one launch (default 4096; the
+ * scratch space grows with it).  1 gives the one-gate-per-launch form. */
+int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
+
+/* Blind-rotation kernel variants (same results, different register/occupancy
+ * trade-offs): 0..MK_NUM_VARIANTS-1.  mk_autotune times every variant on
+ * `sample_gates` random ciphertexts on the context's device, keeps the
+ * fastest for the context and stores it in *best (and, if ms_out is not
+ * NULL, each variant's milliseconds in ms_out[0..MK_NUM_VARIANTS-1]).  It
+ * synchronises the stream.  No paper counterpart: a tuning aid. */
+#define MK_NUM_VARIANTS 4
+int mk_ctx_set_variant(mk_ctx *ctx, int variant);
+int mk_ctx_get_variant(const mk_ctx *ctx, int *variant);
+int mk_autotune(mk_ctx *ctx, uint32_t sample_gates, int *best, float *ms_out);
+
+/* Message of the last failed call on ctx (never NULL). */
+const char *mk_last_error(const mk_ctx *ctx);
+
+/* Wait for all work enqueued on the context's stream; reports any
+ * asynchronous CUDA error as MK_EDEVICE. */
+int mk_sync(mk_ctx *ctx);
+
+/* ---------------------------------------------------------------- keys */
+/* MKTFHE.KeyGen (Sec. 2.2) for party `party` (0-based) from `seed`: the TLWE
+ * secret s in {0,1}^n, the RLWE secret z in {0,1}^N, the public key
+ * b = -z*a + e, the bootstrapping key BK = {UniEnc(s_j; z)}_j and the
+ * key-switching key KS.  Secrets stay in host memory of the context; public
+ * material is uploaded on first use.  Deterministic in (params, crs_seed,
+ * seed): every random number comes from Philox4x32-10 streams. */
+int mk_keygen(mk_ctx *ctx, uint32_t party, uint64_t seed);
+
+/* Key material in host memory, uint32 torus words, row-major:
+ *   crs [d][N];  s [n] (0/1);  z [N] (0/1);  pk [d][N];
+ *   bk  [n][3][d][N]       UniEnc(s_j; z) = (d-vector, f0, f1) for j < n;
+ *   ks  [N][t][B'-1][n+1]  row (a_0..a_{n-1}, b) = LWE_s(delta*z_j*2^(32-ks_bit*(l+1)))
+ *                          at [j][l][delta-1].
+ * mk_import_crs replaces the CRS; mk_import_party copies one party's keys in
+ * (s and z may be NULL for a party whose secrets this context must not hold).
+ * mk_export_* copy out; any output pointer may be NULL to skip that part. */
+int mk_import_crs(mk_ctx *ctx, const uint32_t *h_crs);
+int mk_import_party(mk_ctx *ctx, uint32_t party, const uint32_t *h_s, const uint32_t *h_z,
+                    const uint32_t *h_pk, const uint32_t *h_bk, const uint32_t *h_ks);
+int mk_export_crs(const mk_ctx *ctx, uint32_t *h_crs);
+int mk_export_party(const mk_ctx *ctx, uint32_t party, uint32_t *h_s, uint32_t *h_z, uint32_t *h_pk,
+                    uint32_t *h_bk, uint32_t *h_ks);
+
+/* Serialised key set: header (magic, version, params, party mask, secret
+ * flag), CRS, each party's keys, FNV-1a 64 checksum.  mk_save_keys with
+ * h_blob == NULL stores the needed size in *len.  include_secrets = 0 writes
+ * the public material only.  mk_load_keys returns MK_EFORMAT on a bad magic,
+ * parameter mismatch, truncated blob or checksum. */
+int mk_save_keys(const mk_ctx *ctx, int include_secrets, void *h_blob, size_t cap, size_t *len);
+int mk_load_keys(mk_ctx *ctx, const void *h_blob, size_t len);
+
+/* ---------------------------------------------------------------- enc/dec */
+/* MKTFHE.SymEnc (Sec. 2.2) by party `party` of count bits (0/1 bytes) into
+ * h_ct [count][k*n + 1], extended to the multi-key layout (other parties'
+ * blocks zero).  b = -<a, s> + m/4 + e; a and e from Philox streams of seed. */
+int mk_encrypt(mk_ctx *ctx, uint32_t party, const uint8_t *h_bits, size_t count, uint64_t seed,
+               uint32_t *h_ct);
+/* Encryption under the joint key (every party block uniform); needs every
+ * party's secret.  Used to make all k*n blind-rotation steps active. */
+int mk_encrypt_joint(mk_ctx *ctx, const uint8_t *h_bits, size_t count, uint64_t seed, uint32_t *h_ct);
+
+/* MKTFHE.SymDec (Sec. 2.2): with every party's secret, the bit m minimising
+ * |b + sum_i <a_i, s_i> - m/4|.  `ct` is a host pointer if on_device == 0,
+ * else a device pointer (copied back, synchronising the stream). */
+int mk_decrypt(mk_ctx *ctx, const uint32_t *ct, size_t count, int on_device, uint8_t *h_bits);
+/* Phases b + sum_i <a_i, s_i> of count ciphertexts (same pointer rule). */
+int mk_phase(mk_ctx *ctx, const uint32_t *ct, size_t count, int on_device, uint32_t *h_phase);
+
+/* ---------------------------------------------------------------- gates */
+enum { MK_AND = 0, MK_OR = 1, MK_NAND = 2, MK_NOR = 3, MK_XOR = 4, MK_XNOR = 5 };
+
+/* Multi-key bootstrapped gates (Sec. 3.1): for g < count,
+ *   d_out[g] = KeySwitch(GB(lin(type, d_a[g], d_b[g])))
+ * with the linear part of Eq. 6 (AND), Eq. 7 (OR), Sec. 2.2 (NAND: 5/8 - c1 - c2),
+ * Eq. 9 (NOR, constant 3/8), Eq. 10 (XOR), Eq. 11 (XNOR: 1/2 + 2(c1 - c2)).
+ * mk_gate applies one type to every gate; mk_gates reads a per-gate type
+ * (uint8, device).  d_out may not alias d_a or d_b.  Needs every party's
+ * public keys. */
+int mk_gate(mk_ctx *ctx, int type, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+            size_t count);
+int mk_gates(mk_ctx *ctx, const uint8_t *d_types, const uint32_t *d_a, const uint32_t *d_b,
+             uint32_t *d_out, size_t count);
+
+/* General linear gate: d_out[g] = KeySwitch(GB((0, cst[g]) + s1[g]*a[g] + s2[g]*b[g]))
+ * where d_lin holds count records {uint32 cst; int32 s1; int32 s2} (device). */
+typedef struct mk_lin { uint32_t cst; int32_t s1, s2; } mk_lin;
+int mk_gates_lin(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b,
+                 uint32_t *d_out, size_t count);
+
+/* MKNOT (Eq. 8): d_out[g] = (0, 1/4) - d_a[g]; no bootstrapping, no key
+ * switching.  d_out may alias d_a. */
+int mk_not(mk_ctx *ctx, const uint32_t *d_a, uint32_t *d_out, size_t count);
+
+/* ---------------------------------------------------------------- stages */
+/* The stages of one bootstrapped gate, for stage-by-stage comparison.
+ * mk_stage_modswitch: d_abar[g] = mod-switched words of lin(...) with the
+ *   -1/4 window shift on b (values in [0, 2N)), layout as a ciphertext.
+ * mk_stage_blind_rotate: accumulator (k+1 polynomials of N words) after the
+ *   first max_steps CMux steps (-1 = all k*n), from d_abar.
+ * mk_stage_bootstrap: d_ext[g] = SampleExtract(blind rotation) + 1/8, an LWE
+ *   of dimension k*N + 1 under (z_1..z_k).
+ * mk_stage_keyswitch: MKKeySwitch (Sec. 2.2) of d_ext into d_out. */
+int mk_stage_modswitch(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b,
+                       uint32_t *d_abar, size_t count);
+int mk_stage_blind_rotate(mk_ctx *ctx, const uint32_t *d_abar, size_t count, int64_t max_steps,
+                          uint32_t *d_acc);
+int mk_stage_bootstrap(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b,
+                       uint32_t *d_ext, size_t count);
+int mk_stage_keyswitch(mk_ctx *ctx, const uint32_t *d_ext, uint32_t *d_out, size_t count);
+
+/* ---------------------------------------------------------------- measurement */
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch of the given kernel class while enabled.  mk_timing_read
+ * synchronises the stream and returns the summed device milliseconds and the
+ * launch count since the last reset. */
+enum { MK_KERNEL_BOOTSTRAP = 0, MK_KERNEL_KEYSWITCH = 1 };
+int mk_timing_enable(mk_ctx *ctx, int on);
+int mk_timing_reset(mk_ctx *ctx);
+int mk_timing_read(mk_ctx *ctx, int kernel, double *ms_total, uint64_t *launches);
+
+/* ALU ceiling of the NTT form: run a register-resident loop of independent
+ * Goldilocks butterflies (one 64-bit modular multiply, add and subtract each)
+ * on every SM of `device`; *per_s receives butterflies per second.  No paper
+ * counterpart: a measurement aid for the roofline of the blind rotation. */
+int mk_measure_butterfly_rate(int device, void *stream, uint32_t iters, double *per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MK_TFHE_H */

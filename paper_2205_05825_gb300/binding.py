@@ -1,0 +1,365 @@
+"""Thin ctypes binding of ``libmktfhe.so`` (the C ABI in include/mk_tfhe.h).
+
+Argument marshalling only: every step of a gate runs in the library's CUDA
+kernels.  Device buffers are torch tensors (uint32 as torch.int32 storage);
+host buffers are numpy arrays.  Loading fails loudly when the library has not
+been built -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MK_OK = 0
+ERRORS = {-1: "MK_EINVAL", -2: "MK_ENOMEM", -3: "MK_EPARAMS", -4: "MK_ETIMEOUT", -5: "MK_EDEVICE",
+          -6: "MK_ESTATE", -7: "MK_EFORMAT"}
+GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
+PRESETS = {"toy": 0, "full": 1, "paper": 2}
+NUM_VARIANTS = 4
+
+U32P = ctypes.POINTER(ctypes.c_uint32)
+U8P = ctypes.POINTER(ctypes.c_uint8)
+VP = ctypes.c_void_p
+
+
+class MkParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("N", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("bg_bit", ctypes.c_uint32), ("d", ctypes.c_uint32), ("ks_bit", ctypes.c_uint32),
+                ("t", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("sigma_lwe", ctypes.c_double), ("sigma_rlwe", ctypes.c_double)]
+
+    @classmethod
+    def from_dict(cls, p):
+        return cls(p["n"], p["N"], p["k"], p["bg_bit"], p["d"], p["ks_bit"], p["t"], 0,
+                   float(p["sigma_lwe"]), float(p["sigma_rlwe"]))
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class MkLin(ctypes.Structure):
+    _fields_ = [("cst", ctypes.c_uint32), ("s1", ctypes.c_int32), ("s2", ctypes.c_int32)]
+
+
+class MkError(RuntimeError):
+    pass
+
+
+_SIGS = {
+    "mk_params_preset": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(MkParams)]),
+    "mk_ctx_create": (ctypes.c_int, [ctypes.POINTER(MkParams), ctypes.c_uint64, ctypes.c_int, VP,
+                                     ctypes.POINTER(VP)]),
+    "mk_ctx_destroy": (ctypes.c_int, [VP]),
+    "mk_ctx_set_stream": (ctypes.c_int, [VP, VP]),
+    "mk_ctx_get_params": (ctypes.c_int, [VP, ctypes.POINTER(MkParams)]),
+    "mk_ctx_set_form": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_ctx_set_batch": (ctypes.c_int, [VP, ctypes.c_uint32]),
+    "mk_last_error": (ctypes.c_char_p, [VP]),
+    "mk_sync": (ctypes.c_int, [VP]),
+    "mk_keygen": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint64]),
+    "mk_import_crs": (ctypes.c_int, [VP, U32P]),
+    "mk_import_party": (ctypes.c_int, [VP, ctypes.c_uint32, U32P, U32P, U32P, U32P, U32P]),
+    "mk_export_crs": (ctypes.c_int, [VP, U32P]),
+    "mk_export_party": (ctypes.c_int, [VP, ctypes.c_uint32, U32P, U32P, U32P, U32P, U32P]),
+    "mk_save_keys": (ctypes.c_int, [VP, ctypes.c_int, VP, ctypes.c_size_t,
+                                    ctypes.POINTER(ctypes.c_size_t)]),
+    "mk_load_keys": (ctypes.c_int, [VP, VP, ctypes.c_size_t]),
+    "mk_encrypt": (ctypes.c_int, [VP, ctypes.c_uint32, U8P, ctypes.c_size_t, ctypes.c_uint64, U32P]),
+    "mk_encrypt_joint": (ctypes.c_int, [VP, U8P, ctypes.c_size_t, ctypes.c_uint64, U32P]),
+    "mk_decrypt": (ctypes.c_int, [VP, VP, ctypes.c_size_t, ctypes.c_int, U8P]),
+    "mk_phase": (ctypes.c_int, [VP, VP, ctypes.c_size_t, ctypes.c_int, U32P]),
+    "mk_gate": (ctypes.c_int, [VP, ctypes.c_int, VP, VP, VP, ctypes.c_size_t]),
+    "mk_gates": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
+    "mk_gates_lin": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
+    "mk_not": (ctypes.c_int, [VP, VP, VP, ctypes.c_size_t]),
+    "mk_stage_modswitch": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
+    "mk_stage_blind_rotate": (ctypes.c_int, [VP, VP, ctypes.c_size_t, ctypes.c_int64, VP]),
+    "mk_stage_bootstrap": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
+    "mk_stage_keyswitch": (ctypes.c_int, [VP, VP, VP, ctypes.c_size_t]),
+    "mk_ctx_set_variant": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_ctx_get_variant": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
+    "mk_autotune": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_float)]),
+    "mk_timing_enable": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_timing_reset": (ctypes.c_int, [VP]),
+    "mk_timing_read": (ctypes.c_int, [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "mk_measure_butterfly_rate": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_uint32,
+                                                 ctypes.POINTER(ctypes.c_double)]),
+}
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load the CUDA library; raise if it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise MkError("libmktfhe.so is not built (%s); run __graft_entry__.build()" % path)
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def preset(name, k):
+    p = MkParams()
+    rc = load().mk_params_preset(PRESETS[name], k, ctypes.byref(p))
+    if rc != MK_OK:
+        raise MkError("mk_params_preset: %s" % ERRORS.get(rc, rc))
+    return p.as_dict()
+
+
+def _np_u32(a):
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return a, a.ctypes.data_as(U32P)
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (marshalling only)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise MkError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def key_shapes(params):
+    n, N, k, d, t = params["n"], params["N"], params["k"], params["d"], params["t"]
+    nb = (1 << params["ks_bit"]) - 1
+    return dict(crs=(d, N), s=(n,), z=(N,), pk=(d, N), bk=(n, 3, d, N), ks=(N, t, nb, n + 1))
+
+
+class Context:
+    """One mk_ctx: parameters, keys, device and stream."""
+
+    def __init__(self, params, crs_seed, device=0, stream=None):
+        self.L = load()
+        self.params = dict(params)
+        self._p = MkParams.from_dict(params)
+        h = VP()
+        if stream is None and device >= 0:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        rc = self.L.mk_ctx_create(ctypes.byref(self._p), crs_seed, device,
+                                  ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if rc != MK_OK:
+            raise MkError("mk_ctx_create: %s" % ERRORS.get(rc, rc))
+        self.h = h
+        self.device = device
+        self.W = params["k"] * params["n"] + 1
+        self.E = params["k"] * params["N"] + 1
+
+    def close(self):
+        if self.h:
+            self.L.mk_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != MK_OK:
+            msg = self.L.mk_last_error(self.h).decode()
+            raise MkError("%s: %s (%s)" % (what, ERRORS.get(rc, rc), msg))
+
+    # ---------------------------------------------------------------- settings
+    def set_stream(self, stream):
+        self._check(self.L.mk_ctx_set_stream(self.h, ctypes.c_void_p(stream or 0)), "mk_ctx_set_stream")
+
+    def set_batch(self, n):
+        self._check(self.L.mk_ctx_set_batch(self.h, n), "mk_ctx_set_batch")
+
+    def set_form(self, form):
+        self._check(self.L.mk_ctx_set_form(self.h, form), "mk_ctx_set_form")
+
+    def set_variant(self, v):
+        self._check(self.L.mk_ctx_set_variant(self.h, v), "mk_ctx_set_variant")
+
+    def get_variant(self):
+        v = ctypes.c_int()
+        self._check(self.L.mk_ctx_get_variant(self.h, ctypes.byref(v)), "mk_ctx_get_variant")
+        return v.value
+
+    def autotune(self, sample_gates):
+        """Time every blind-rotation variant; keep the fastest. -> (best, [ms per variant])."""
+        best = ctypes.c_int()
+        ms = (ctypes.c_float * NUM_VARIANTS)()
+        self._check(self.L.mk_autotune(self.h, sample_gates, ctypes.byref(best), ms), "mk_autotune")
+        return best.value, list(ms)
+
+    def sync(self):
+        self._check(self.L.mk_sync(self.h), "mk_sync")
+
+    # ---------------------------------------------------------------- keys
+    def keygen(self, party, seed):
+        self._check(self.L.mk_keygen(self.h, party, seed), "mk_keygen")
+
+    def import_crs(self, crs):
+        a, p = _np_u32(crs)
+        self._check(self.L.mk_import_crs(self.h, p), "mk_import_crs")
+
+    def import_party(self, party, s, z, pk, bk, ks):
+        arrs = [(_np_u32(x) if x is not None else (None, None)) for x in (s, z, pk, bk, ks)]
+        self._check(self.L.mk_import_party(self.h, party, *[a[1] for a in arrs]), "mk_import_party")
+
+    def import_oracle_keys(self, keys, with_secrets=True):
+        """Copy a key set (numpy arrays, layouts of include/mk_tfhe.h) in."""
+        self.import_crs(keys.crs)
+        for i in range(self.params["k"]):
+            self.import_party(i, keys.s[i] if with_secrets else None, keys.z[i] if with_secrets else None,
+                              keys.pk[i], keys.bk[i], keys.ks[i])
+
+    def export_crs(self):
+        out = np.zeros(key_shapes(self.params)["crs"], np.uint32)
+        self._check(self.L.mk_export_crs(self.h, out.ctypes.data_as(U32P)), "mk_export_crs")
+        return out
+
+    def export_party(self, party, parts=("s", "z", "pk", "bk", "ks")):
+        sh = key_shapes(self.params)
+        outs = {nm: np.zeros(sh[nm], np.uint32) for nm in parts}
+        ptrs = [outs[nm].ctypes.data_as(U32P) if nm in outs else None for nm in ("s", "z", "pk", "bk", "ks")]
+        self._check(self.L.mk_export_party(self.h, party, *ptrs), "mk_export_party")
+        return outs
+
+    def save_keys(self, include_secrets=True):
+        n = ctypes.c_size_t()
+        self._check(self.L.mk_save_keys(self.h, int(include_secrets), None, 0, ctypes.byref(n)), "mk_save_keys")
+        buf = np.zeros(n.value, np.uint8)
+        self._check(self.L.mk_save_keys(self.h, int(include_secrets), buf.ctypes.data_as(VP), n.value,
+                                        ctypes.byref(n)), "mk_save_keys")
+        return buf
+
+    def load_keys(self, blob):
+        blob = np.ascontiguousarray(blob, np.uint8)
+        self._check(self.L.mk_load_keys(self.h, blob.ctypes.data_as(VP), blob.size), "mk_load_keys")
+
+    # ---------------------------------------------------------------- enc / dec
+    def encrypt(self, party, bits, seed):
+        bits = np.ascontiguousarray(bits, np.uint8)
+        out = np.zeros((len(bits), self.W), np.uint32)
+        self._check(self.L.mk_encrypt(self.h, party, bits.ctypes.data_as(U8P), len(bits), seed,
+                                      out.ctypes.data_as(U32P)), "mk_encrypt")
+        return out
+
+    def encrypt_joint(self, bits, seed):
+        bits = np.ascontiguousarray(bits, np.uint8)
+        out = np.zeros((len(bits), self.W), np.uint32)
+        self._check(self.L.mk_encrypt_joint(self.h, bits.ctypes.data_as(U8P), len(bits), seed,
+                                            out.ctypes.data_as(U32P)), "mk_encrypt_joint")
+        return out
+
+    def _ct_arg(self, ct):
+        if isinstance(ct, np.ndarray):
+            ct = np.ascontiguousarray(ct, np.uint32)
+            return ct, ct.ctypes.data_as(VP), ct.size // self.W, 0
+        return ct, _dptr(ct), ct.numel() // self.W, 1
+
+    def decrypt(self, ct):
+        keep, ptr, count, dev = self._ct_arg(ct)
+        out = np.zeros(count, np.uint8)
+        self._check(self.L.mk_decrypt(self.h, ptr, count, dev, out.ctypes.data_as(U8P)), "mk_decrypt")
+        return out
+
+    def phase(self, ct):
+        keep, ptr, count, dev = self._ct_arg(ct)
+        out = np.zeros(count, np.uint32)
+        self._check(self.L.mk_phase(self.h, ptr, count, dev, out.ctypes.data_as(U32P)), "mk_phase")
+        return out
+
+    # ---------------------------------------------------------------- gates (device tensors)
+    def gate(self, gate, a, b, out):
+        ty = GATES[gate] if isinstance(gate, str) else int(gate)
+        self._check(self.L.mk_gate(self.h, ty, _dptr(a), _dptr(b), _dptr(out), a.numel() // self.W), "mk_gate")
+        return out
+
+    def gates(self, types, a, b, out):
+        self._check(self.L.mk_gates(self.h, _dptr(types), _dptr(a), _dptr(b), _dptr(out), types.numel()),
+                    "mk_gates")
+        return out
+
+    def gates_lin(self, lin, a, b, out):
+        """lin: CUDA int32 tensor [count, 3] of (cst, s1, s2)."""
+        self._check(self.L.mk_gates_lin(self.h, _dptr(lin), _dptr(a), _dptr(b), _dptr(out), lin.shape[0]),
+                    "mk_gates_lin")
+        return out
+
+    def mk_not(self, a, out):
+        self._check(self.L.mk_not(self.h, _dptr(a), _dptr(out), a.numel() // self.W), "mk_not")
+        return out
+
+    # ---------------------------------------------------------------- measurement
+    def timing_enable(self, on=True):
+        self._check(self.L.mk_timing_enable(self.h, int(on)), "mk_timing_enable")
+
+    def timing_reset(self):
+        self._check(self.L.mk_timing_reset(self.h), "mk_timing_reset")
+
+    def timing_read(self, kernel):
+        """kernel: 0 = blind rotation (bootstrap), 1 = key switch -> (ms_total, launches)."""
+        ms, n = ctypes.c_double(), ctypes.c_uint64()
+        self._check(self.L.mk_timing_read(self.h, kernel, ctypes.byref(ms), ctypes.byref(n)), "mk_timing_read")
+        return ms.value, n.value
+
+    # ---------------------------------------------------------------- stages
+    def stage_modswitch(self, lin, a, b, abar):
+        self._check(self.L.mk_stage_modswitch(self.h, _dptr(lin), _dptr(a), _dptr(b), _dptr(abar), lin.shape[0]),
+                    "mk_stage_modswitch")
+        return abar
+
+    def stage_blind_rotate(self, abar, max_steps, acc):
+        self._check(self.L.mk_stage_blind_rotate(self.h, _dptr(abar), abar.numel() // self.W, max_steps,
+                                                 _dptr(acc)), "mk_stage_blind_rotate")
+        return acc
+
+    def stage_bootstrap(self, lin, a, b, ext):
+        self._check(self.L.mk_stage_bootstrap(self.h, _dptr(lin), _dptr(a), _dptr(b), _dptr(ext), lin.shape[0]),
+                    "mk_stage_bootstrap")
+        return ext
+
+    def stage_keyswitch(self, ext, out):
+        self._check(self.L.mk_stage_keyswitch(self.h, _dptr(ext), _dptr(out), ext.numel() // self.E),
+                    "mk_stage_keyswitch")
+        return out
+
+
+# Linear-part records (cst, s1, s2) of the six bootstrapped gates, for
+# mk_gates_lin: Eq. 6 (AND), Eq. 7 (OR), Sec. 2.2 (NAND), Eq. 9 (NOR, 3/8),
+# Eq. 10 (XOR), Eq. 11 (XNOR, 1/2 + 2(c1 - c2)).
+GATE_LIN = {0: (0xE0000000, 1, 1), 1: (0x20000000, 1, 1), 2: (0xA0000000, -1, -1),
+            3: (0x60000000, -1, -1), 4: (0, 2, -2), 5: (0x80000000, 2, -2)}
+
+
+def lin_records(types):
+    """numpy int32 [count, 3] of (cst, s1, s2) for gate types (int array)."""
+    rec = np.array([GATE_LIN[int(t)] for t in types], dtype=np.int64).reshape(-1, 3)
+    out = np.zeros((len(types), 3), np.int32)
+    out[:, 0] = rec[:, 0].astype(np.uint32).view(np.int32)
+    out[:, 1:] = rec[:, 1:]
+    return out
+
+
+def measure_butterfly_rate(device=0, stream=None, iters=4096):
+    """Goldilocks butterflies per second on every SM (ALU ceiling of the NTT form)."""
+    r = ctypes.c_double()
+    rc = load().mk_measure_butterfly_rate(device, ctypes.c_void_p(stream or 0), iters, ctypes.byref(r))
+    if rc != MK_OK:
+        raise MkError("mk_measure_butterfly_rate: %s" % ERRORS.get(rc, rc))
+    return r.value

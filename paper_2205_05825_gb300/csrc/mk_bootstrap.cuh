@@ -1,0 +1,478 @@
+// mk_bootstrap.cuh -- device building blocks of the blind rotation (NTT form).
+// Included by one translation unit per ring dimension (mk_br_<N>.cu) so that
+// the template instantiations compile in parallel.
+//
+// One CTA owns one gate for the whole blind rotation ("CTA-owns-gate"): the
+// accumulator ACC (k+1 polynomials of N torus32 words) lives in shared memory
+// for all k*n CMux steps, so the only L2/HBM traffic per step is the
+// bootstrapping-key entry BK_{i,j} (3*d polynomials in the NTT domain) and the
+// public keys.  Negacyclic products are exact: a negacyclic NTT over the
+// Goldilocks prime p = 2^64 - 2^32 + 1, whose half exceeds every product sum
+// (|sum| < (k+1) * d * N * 2^7 * 2^32 < 2^55), so the integer result is
+// recovered exactly and reduced mod 2^32 -- bit-identical to schoolbook
+// wrapping uint32 arithmetic.
+//
+// Code size is a first-order cost here: the step body runs k*n times per gate
+// and an unrolled 1024-point NTT per call site does not fit the instruction
+// caches.  So each transform direction has exactly one call site inside the
+// CMux loop, and its passes run in a rolled loop (three radix-2 stages per
+// pass in registers, compile-time butterfly patterns D = 4, 2, 1).
+//
+// Paper steps (arXiv 2205.05825): gate linear part (Sec. 3.1, Eq. 6-11,
+// Algorithms 1-2), gate bootstrapping GB (Sec. 2.2).  The hybrid product
+// follows the MKTFHE construction the paper builds on (named in Sec. 2.2):
+// u_j = g^-1(c_j); v = -<u_0, a> + sum_{j>=1} <u_j, pk_j>; w = g^-1(v);
+// c'_j = <u_j, d>; c'_0 += <w, f0>; c'_i += <w, f1>.
+#pragma once
+#include "mk_internal.h"
+
+namespace mk {
+namespace br {
+
+constexpr uint64_t P = kGoldilocks;
+constexpr uint64_t EPS = 0xFFFFFFFFull;  // 2^64 mod p
+constexpr uint64_t HALF_P = P >> 1;
+
+// ------------------------------------------------------------ Goldilocks field
+// Values are kept in [0, 2^64), congruent mod p but not always below p; the
+// multiply reduces any 128-bit product and returns a canonical value (< p).
+// add1/sub1 need their second operand canonical; add2/sub2 take any operands.
+__device__ __forceinline__ uint64_t gmul(uint64_t a, uint64_t b) {
+    const uint64_t lo = a * b;
+    const uint64_t hi = __umul64hi(a, b);
+    const uint64_t hh = hi >> 32, hl = hi & EPS;
+    // x = lo + hl * 2^64 + hh * 2^96 = lo + hl * (2^32 - 1) - hh  (mod p)
+    uint64_t t0 = lo - hh;
+    t0 = (lo < hh) ? t0 - EPS : t0;
+    const uint64_t t1 = hl * EPS;
+    uint64_t r = t0 + t1;
+    r = (r < t1) ? r + EPS : r;
+    return (r >= P) ? r - P : r;
+}
+
+// a + b with b < p: one wrap (2^64 = EPS mod p) cannot overflow again.
+__device__ __forceinline__ uint64_t add1(uint64_t a, uint64_t b) {
+    const uint64_t s = a + b;
+    return (s < b) ? s + EPS : s;
+}
+
+// a - b with b < p: the borrow correction (add p = subtract EPS) cannot underflow.
+__device__ __forceinline__ uint64_t sub1(uint64_t a, uint64_t b) {
+    const uint64_t d = a - b;
+    return (a < b) ? d - EPS : d;
+}
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t s = a + b;
+    if (s < a) {
+        s += EPS;
+        if (s < EPS) s += EPS;
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d = a - b;
+    if (a < b) {
+        const uint64_t e = d - EPS;
+        d = (d < EPS) ? e - EPS : e;
+    }
+    return d;
+}
+
+__device__ __forceinline__ uint64_t digit_to_field(int32_t u) {
+    return u >= 0 ? (uint64_t)u : P - (uint64_t)(-(int64_t)u);
+}
+
+// Field element (any representative < 2^64) of an exact integer in
+// (-p/2, p/2) -> that integer mod 2^32 (p = 1 mod 2^32).
+__device__ __forceinline__ uint32_t field_to_u32(uint64_t y) {
+    if (y >= P) y -= P;
+    return (uint32_t)y - (y > HALF_P ? 1u : 0u);
+}
+
+__device__ __forceinline__ void load8(const uint64_t *__restrict__ src, uint64_t (&v)[8]) {
+    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ulonglong2 t = __ldg(s2 + q);
+        v[2 * q] = t.x;
+        v[2 * q + 1] = t.y;
+    }
+}
+
+// ------------------------------------------------------------ negacyclic NTT
+// Thread `tid` (of N/8) holds 8 elements per polynomial.  A pass processes up
+// to three consecutive butterfly stages in registers; its 8 elements are the
+// indices whose bits [LO, LO+3) vary:  j = base(tid, LO) | c << LO with
+// base = tid[0,LO) | tid[LO,..) << (LO+3).
+// Forward (Cooley-Tukey, twist folded into psi^bitrev): input natural order in
+// layout LO = logN-3 (coefficient tid + (N/8)*c), output bit-reversed order in
+// layout LO = 0 (index 8*tid + c).  Inverse (Gentleman-Sande) goes back, and
+// omits the 1/N factor (the keys carry it).  Between passes the elements move
+// through padded shared memory (one pad word every 16 keeps each 64-bit warp
+// access at the 2-wavefront minimum).
+__device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }
+
+__device__ __forceinline__ int jbase(int tid, int LO) {
+    return (tid & ((1 << LO) - 1)) | ((tid >> LO) << (LO + 3));
+}
+
+template <int LOGN>
+struct Ntt {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int T = N / 8;
+    static constexpr int PN = N + N / 16;  // padded polynomial stride in xbuf
+
+    // Forward stage at bit b (distance 2^b) inside a pass with element bits
+    // [LO, LO+3): element pairs (c, c + D), D = 2^(b - LO).
+    template <int NP, int D>
+    __device__ static __forceinline__ void fwd_stage(uint64_t (&x)[NP][8], int jb, int LO, int b,
+                                                     const uint64_t *tw) {
+        const int m = 1 << (LOGN - 1 - b);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c & D) continue;
+            const uint64_t S = tw[m + ((jb | (c << LO)) >> (b + 1))];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const uint64_t U = x[p][c];
+                const uint64_t V = gmul(x[p][c + D], S);
+                x[p][c] = add1(U, V);
+                x[p][c + D] = sub1(U, V);
+            }
+        }
+    }
+
+    template <int NP, int D>
+    __device__ static __forceinline__ void inv_stage(uint64_t (&x)[NP][8], int jb, int LO, int b,
+                                                     const uint64_t *tw) {
+        const int m = 1 << (LOGN - 1 - b);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c & D) continue;
+            const uint64_t S = tw[m + ((jb | (c << LO)) >> (b + 1))];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const uint64_t U = x[p][c];
+                const uint64_t V = x[p][c + D];
+                x[p][c] = add2(U, V);
+                x[p][c + D] = gmul(sub2(U, V), S);
+            }
+        }
+    }
+
+    template <int NP>
+    __device__ static __forceinline__ void exchange(uint64_t (&x)[NP][8], int tid, uint64_t *buf, int LOf, int LOt) {
+        const int bf = jbase(tid, LOf);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) buf[p * PN + pidx(bf | (c << LOf))] = x[p][c];
+        __syncthreads();
+        const int bt = jbase(tid, LOt);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[p][c] = buf[p * PN + pidx(bt | (c << LOt))];
+        __syncthreads();
+    }
+
+    // natural (layout logN-3) -> bit-reversed (layout 0)
+    template <int NP>
+    __device__ static __forceinline__ void forward(uint64_t (&x)[NP][8], int tid, const uint64_t *tw, uint64_t *buf) {
+        int prev = LOGN - 3;
+#pragma unroll 1
+        for (int hi = LOGN - 1; hi >= 0; hi -= 3) {
+            const int LO = hi >= 2 ? hi - 2 : 0;
+            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO);
+            const int jb = jbase(tid, LO);
+            if (hi - LO == 2) fwd_stage<NP, 4>(x, jb, LO, LO + 2, tw);
+            if (hi - LO >= 1) fwd_stage<NP, 2>(x, jb, LO, LO + 1, tw);
+            fwd_stage<NP, 1>(x, jb, LO, LO, tw);
+            prev = LO;
+        }
+    }
+
+    // bit-reversed (layout 0) -> natural (layout logN-3), without 1/N
+    template <int NP>
+    __device__ static __forceinline__ void inverse(uint64_t (&x)[NP][8], int tid, const uint64_t *tw, uint64_t *buf) {
+        int prev = 0;
+#pragma unroll 1
+        for (int lo = 0; lo < LOGN; lo += 3) {
+            const int hi = (lo + 2 < LOGN - 1) ? lo + 2 : LOGN - 1;
+            const int LO = (lo < LOGN - 3) ? lo : LOGN - 3;
+            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO);
+            const int jb = jbase(tid, LO);
+            if (lo == LO) inv_stage<NP, 1>(x, jb, LO, LO, tw);
+            if (lo <= LO + 1 && hi >= LO + 1) inv_stage<NP, 2>(x, jb, LO, LO + 1, tw);
+            if (hi == LO + 2) inv_stage<NP, 4>(x, jb, LO, LO + 2, tw);
+            prev = LO;
+        }
+    }
+};
+
+// ------------------------------------------------------------ gadget g^-1
+// Signed base-2^bg digits with round-to-nearest at the last digit (d = 3).
+struct Gadget {
+    uint32_t offset;
+    uint32_t bg_bit;
+    uint32_t mask, half;
+    __device__ __forceinline__ uint64_t digit(uint32_t x, int l) const {
+        const uint32_t xp = x + offset;
+        return digit_to_field((int32_t)((xp >> (32 - bg_bit * (l + 1))) & mask) - (int32_t)half);
+    }
+};
+
+__device__ __forceinline__ Gadget make_gadget(uint32_t bg_bit) {
+    Gadget g;
+    g.bg_bit = bg_bit;
+    g.mask = (1u << bg_bit) - 1;
+    g.half = 1u << (bg_bit - 1);
+    uint32_t off = 0;
+    for (uint32_t l = 1; l <= 3; ++l) off += g.half << (32 - bg_bit * l);
+    if (3 * bg_bit < 32) off += 1u << (32 - 3 * bg_bit - 1);
+    g.offset = off;
+    return g;
+}
+
+// ------------------------------------------------------------ blind rotation
+struct SmemLayout {
+    size_t twf, twi, xbuf, acc, abar, total;
+};
+
+template <int LOGN, int NPF>
+__host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
+    constexpr int N = 1 << LOGN;
+    SmemLayout L;
+    L.twf = 0;
+    L.twi = L.twf + sizeof(uint64_t) * N;
+    L.xbuf = L.twi + sizeof(uint64_t) * N;
+    L.acc = L.xbuf + sizeof(uint64_t) * NPF * (N + N / 16);
+    L.abar = L.acc + sizeof(uint32_t) * (k + 1) * N;
+    L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
+    return L;
+}
+
+template <int NP>
+__device__ __forceinline__ void mac8(uint64_t (&A)[8], const uint64_t (&x)[8], const uint64_t *__restrict__ key,
+                                     int tid) {
+    uint64_t kv[8];
+    load8(key + tid * 8, kv);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) A[c] = add1(A[c], gmul(x[c], kv[c]));
+}
+
+// One CMux step for party i (1..k) at rotation e:
+//   ACC += HP((X^{-e} - 1) ACC, BK_{i,j}).
+// Slots q = 0..k are the accumulator polynomials in the order 0, i, others
+// (phase A); slot k+1 is phase B (w = g^-1(v) against f0, f1).  NPF digit
+// polynomials go through one forward transform together.
+template <int LOGN, int NPF>
+__device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys &K, const Gadget &G,
+                                          const uint64_t *bk, int i, uint32_t e, uint32_t *acc, uint64_t *xbuf,
+                                          const uint64_t *twf, const uint64_t *twi, int tid) {
+    using NT = Ntt<LOGN>;
+    constexpr int N = NT::N, T = NT::T;
+    const int k = (int)S.k;
+    uint64_t C0[8], CI[8], CJ[8], V[8];
+    uint32_t vv[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) C0[c] = CI[c] = CJ[c] = V[c] = 0;
+#pragma unroll 1
+    for (int q = 0; q <= k + 1; ++q) {
+        const int jj = (q == 0) ? 0 : (q == 1 ? i : (q - 1 < i ? q - 1 : q));  // q <= k only
+        if (q >= 2 && q <= k) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) CJ[c] = 0;
+        }
+#pragma unroll 1
+        for (int l0 = 0; l0 < 3; l0 += NPF) {
+            uint64_t x[NPF][8];
+            if (q <= k) {
+                const uint32_t *ap = acc + jj * N;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t m = tid + T * c;
+                    uint32_t r = m + e;
+                    if (r >= 2 * N) r -= 2 * N;
+                    uint32_t a = ap[r & (N - 1)];
+                    if (r >= N) a = 0u - a;
+                    const uint32_t D = a - ap[m];
+#pragma unroll
+                    for (int p = 0; p < NPF; ++p) x[p][c] = G.digit(D, l0 + p);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+#pragma unroll
+                    for (int p = 0; p < NPF; ++p) x[p][c] = G.digit(vv[c], l0 + p);
+            }
+            NT::template forward<NPF>(x, tid, twf, xbuf);
+#pragma unroll
+            for (int p = 0; p < NPF; ++p) {
+                const int l = l0 + p;
+                if (q <= k) {
+                    const uint64_t *kd = bk + l * N;                              // d_l of BK_{i,j}
+                    const uint64_t *ka = K.keyA + ((size_t)jj * 3 + l) * N;       // -a_l or pk_jj[l]
+                    if (q == 0) mac8<NPF>(C0, x[p], kd, tid);
+                    else if (q == 1) mac8<NPF>(CI, x[p], kd, tid);
+                    else mac8<NPF>(CJ, x[p], kd, tid);
+                    mac8<NPF>(V, x[p], ka, tid);
+                } else {
+                    mac8<NPF>(C0, x[p], bk + (3 + l) * N, tid);  // f0_l
+                    mac8<NPF>(CI, x[p], bk + (6 + l) * N, tid);  // f1_l
+                }
+            }
+        }
+        // Inverse transforms due after this slot, one call site for all:
+        //   kind 0: c'_jj -> ACC_jj   (2 <= q <= k)
+        //   kind 1: v -> registers    (q == k)
+        //   kind 2: c'_0 -> ACC_0, kind 3: c'_i -> ACC_i  (q == k+1)
+        const int first = (q >= 2 && q <= k) ? 0 : (q == k ? 1 : (q == k + 1 ? 2 : 4));
+        const int last = (q == k) ? 1 : (q == k + 1 ? 3 : (q >= 2 ? 0 : -1));
+#pragma unroll 1
+        for (int kind = first; kind <= last; ++kind) {
+            uint64_t y[1][8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                y[0][c] = kind == 0 ? CJ[c] : (kind == 1 ? V[c] : (kind == 2 ? C0[c] : CI[c]));
+            NT::template inverse<1>(y, tid, twi, xbuf);
+            if (kind == 1) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) vv[c] = field_to_u32(y[0][c]);
+            } else {
+                uint32_t *dst = acc + (kind == 0 ? jj : (kind == 2 ? 0 : i)) * N;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) dst[tid + T * c] += field_to_u32(y[0][c]);
+            }
+        }
+    }
+}
+
+// k*n CMux steps (i = 1..k, j = 0..n-1 ascending).
+template <int LOGN, int NPF>
+__device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const DeviceKeys &K, const uint16_t *abar,
+                                                  uint32_t *acc, uint64_t *xbuf, const uint64_t *twf,
+                                                  const uint64_t *twi, int64_t max_steps, int tid) {
+    constexpr int N = 1 << LOGN;
+    const int n = (int)S.n, k = (int)S.k;
+    const Gadget G = make_gadget(S.bg_bit);
+    int64_t steps = 0;
+#pragma unroll 1
+    for (int i = 1; i <= k; ++i) {
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+            if (max_steps >= 0 && steps >= max_steps) return;
+            ++steps;
+            const uint32_t e = abar[(i - 1) * n + j];
+            if (e == 0) continue;  // X^0 - 1 = 0: every digit is 0, HP adds nothing
+            const uint64_t *bk = K.bk + ((size_t)((i - 1) * n + j) * 9) * N;
+            cmux_step<LOGN, NPF>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
+            __syncthreads();
+        }
+    }
+}
+
+template <int LOGN>
+__device__ __forceinline__ void load_twiddles(const DeviceKeys &K, uint64_t *twf, uint64_t *twi, int tid) {
+    constexpr int N = 1 << LOGN, T = N / 8;
+    for (int x = tid; x < N; x += T) {
+        twf[x] = K.tw_fwd[x];
+        twi[x] = K.tw_inv[x];
+    }
+}
+
+// ACC = (X^{-bbar} * v, 0, ..., 0), v = sum_m (1/8) X^m.
+template <int LOGN>
+__device__ __forceinline__ void init_acc(uint32_t *acc, uint32_t k, uint32_t bbar, int tid) {
+    constexpr int N = 1 << LOGN, T = N / 8;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t m = tid + T * c;
+        uint32_t r = m + bbar;
+        if (r >= 2 * N) r -= 2 * N;
+        acc[m] = (r >= (uint32_t)N) ? (0u - (1u << 29)) : (1u << 29);
+    }
+    for (uint32_t x = N + tid; x < (k + 1) * N; x += T) acc[x] = 0;
+}
+
+// Linear part + window shift + modulus switch of one gate into abar (shared).
+__device__ __forceinline__ void lin_modswitch(const LaunchShape &S, const GateDesc &g, const uint32_t *ct_a,
+                                              const uint32_t *ct_b, uint16_t *abar, int tid, int nthreads) {
+    const uint32_t W = S.k * S.n + 1;
+    const uint32_t sh = 32 - (S.logN + 1);
+    const uint32_t *ca = ct_a + (size_t)g.ia * W;
+    const uint32_t *cb = ct_b + (size_t)g.ib * W;
+    for (uint32_t x = tid; x < W; x += nthreads) {
+        uint32_t v = (uint32_t)g.s1 * ca[x] + (uint32_t)g.s2 * cb[x];
+        if (x == W - 1) v += g.cst - (1u << 30);  // (0, cst) and the -1/4 window shift
+        abar[x] = (uint16_t)((v + (1u << (sh - 1))) >> sh);
+    }
+}
+
+template <int LOGN>
+__device__ __forceinline__ void sample_extract(const LaunchShape &S, const uint32_t *acc, uint32_t *dst, int tid) {
+    constexpr int N = 1 << LOGN, T = N / 8;
+    for (uint32_t i = 1; i <= S.k; ++i) {
+        const uint32_t *ci = acc + i * N;
+        uint32_t *ai = dst + (i - 1) * N;
+        for (int m = tid; m < N; m += T) ai[m] = (m == 0) ? ci[0] : 0u - ci[N - m];
+    }
+    if (tid == 0) dst[S.k * N] = acc[0] + (1u << 29);  // +1/8
+}
+
+// One kernel for the whole gate and for the stage entry points:
+//   abar_in == nullptr: linear part + window shift + modulus switch from desc;
+//   otherwise the mod-switched words are read from abar_in.
+//   acc_out == nullptr: SampleExtract + 1/8 into ext; otherwise the raw ACC.
+template <int LOGN, int NPF, int MINB>
+__global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
+bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
+                     const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
+                     const uint32_t *__restrict__ abar_in, int64_t max_steps,
+                     uint32_t *__restrict__ ext, uint32_t *__restrict__ acc_out) {
+    constexpr int N = 1 << LOGN, T = N / 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout<LOGN, NPF>(S.k, S.n);
+    uint64_t *twf = reinterpret_cast<uint64_t *>(smem + L.twf);
+    uint64_t *twi = reinterpret_cast<uint64_t *>(smem + L.twi);
+    uint64_t *xbuf = reinterpret_cast<uint64_t *>(smem + L.xbuf);
+    uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
+    uint16_t *abar = reinterpret_cast<uint16_t *>(smem + L.abar);
+    const int tid = threadIdx.x;
+    load_twiddles<LOGN>(K, twf, twi, tid);
+    if (abar_in) {
+        const uint32_t W = S.k * S.n + 1;
+        for (uint32_t x = tid; x < W; x += T) abar[x] = (uint16_t)abar_in[(size_t)blockIdx.x * W + x];
+    } else {
+        lin_modswitch(S, desc[blockIdx.x], ct_a, ct_b, abar, tid, T);
+    }
+    __syncthreads();
+    init_acc<LOGN>(acc, S.k, abar[S.k * S.n], tid);
+    __syncthreads();
+    blind_rotate_core<LOGN, NPF>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
+    __syncthreads();
+    if (acc_out) {
+        uint32_t *dst = acc_out + (size_t)blockIdx.x * (S.k + 1) * N;
+        for (uint32_t x = tid; x < (S.k + 1) * N; x += T) dst[x] = acc[x];
+    } else {
+        sample_extract<LOGN>(S, acc, ext + (size_t)blockIdx.x * (S.k * N + 1), tid);
+    }
+}
+
+template <int LOGN, int NPF, int MINB>
+cudaError_t launch_bootstrap(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
+                             const uint32_t *ct_a, const uint32_t *ct_b, const uint32_t *abar_in,
+                             int64_t max_steps, uint32_t *ext, uint32_t *acc_out, uint32_t count,
+                             cudaStream_t st) {
+    const SmemLayout L = smem_layout<LOGN, NPF>(S.k, S.n);
+    auto kern = bootstrap_ntt_kernel<LOGN, NPF, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    kern<<<count, (1 << LOGN) / 8, L.total, st>>>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);
+    return cudaGetLastError();
+}
+
+}  // namespace br
+}  // namespace mk

@@ -1,0 +1,24 @@
+// Blind-rotation instantiation for one (ring dimension, variant) pair, chosen
+// by the build with -DMK_LOGN=<log2 N> -DMK_VARIANT=<v>; the variant table is
+// in mk_internal.h.
+#include "mk_bootstrap.cuh"
+
+#ifndef MK_LOGN
+#error "compile with -DMK_LOGN=<log2 N> -DMK_VARIANT=<v>"
+#endif
+
+#define MK_CAT2(a, b, c, d) a##b##c##d
+#define MK_CAT(a, b, c, d) MK_CAT2(a, b, c, d)
+#define MK_FN MK_CAT(launch_bootstrap_logn, MK_LOGN, _v, MK_VARIANT)
+
+namespace mk {
+cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc, const uint32_t *ct_a,
+                  const uint32_t *ct_b, const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,
+                  uint32_t *acc_out, uint32_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    constexpr int NPF = kVariantNpf[MK_VARIANT];
+    constexpr int MINB = kVariantMinBlocks[MK_VARIANT];
+    return br::launch_bootstrap<MK_LOGN, NPF, MINB>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
+                                                    st);
+}
+}  // namespace mk

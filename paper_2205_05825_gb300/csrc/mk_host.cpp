@@ -1,0 +1,1115 @@
+// mk_host.cpp -- host runtime of the multi-key TFHE library: parameters,
+// counter-based randomness, key generation (MKTFHE.Setup / KeyGen, Sec. 2.2
+// of arXiv 2205.05825), SymEnc / SymDec, key layout and upload for the
+// kernels, and the C ABI declared in include/mk_tfhe.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "mk_internal.h"
+
+namespace mk {
+namespace {
+
+// ------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC 2011).  Stream (seed, tag) is the sequence of 32-bit words
+//   word(q) = Philox4x32-10(ctr = (q/4 lo, q/4 hi, tag, 0), key = (seed lo, seed hi))[q % 4].
+struct Philox {
+    static void block(uint32_t c[4], uint32_t k0, uint32_t k1) {
+        for (int r = 0; r < 10; ++r) {
+            const uint64_t m0 = (uint64_t)0xD2511F53u * c[0];
+            const uint64_t m1 = (uint64_t)0xCD9E8D57u * c[2];
+            const uint32_t x0 = (uint32_t)(m1 >> 32) ^ c[1] ^ k0;
+            const uint32_t x2 = (uint32_t)(m0 >> 32) ^ c[3] ^ k1;
+            c[1] = (uint32_t)m1;
+            c[3] = (uint32_t)m0;
+            c[0] = x0;
+            c[2] = x2;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+    uint64_t seed;
+    uint32_t tag;
+    Philox(uint64_t s, uint32_t t) : seed(s), tag(t) {}
+    uint32_t word(uint64_t q) const {
+        const uint64_t blk = q >> 2;
+        uint32_t c[4] = {(uint32_t)blk, (uint32_t)(blk >> 32), tag, 0u};
+        block(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        return c[q & 3];
+    }
+    // Standard normal number q: Box-Muller (cosine branch) on words 2q, 2q+1,
+    // u1 = (w0 + 1) / 2^32, u2 = w1 / 2^32.
+    double normal(uint64_t q) const {
+        const double u1 = ((double)word(2 * q) + 1.0) / 4294967296.0;
+        const double u2 = (double)word(2 * q + 1) / 4294967296.0;
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * 3.14159265358979323846 * u2);
+    }
+    // Torus32 Gaussian noise: round((sigma * 2^32) * g), wrapping.
+    uint32_t gauss32(uint64_t q, double sigma) const {
+        if (sigma == 0.0) return 0u;
+        const double g = normal(q);
+        return (uint32_t)(uint64_t)std::llround(sigma * 4294967296.0 * g);
+    }
+};
+
+enum : uint32_t {
+    kTagCrs = 0x01, kTagS = 0x10, kTagZ = 0x11, kTagPkE = 0x12,
+    kTagBkR = 0x20, kTagBkF1 = 0x21, kTagBkE1 = 0x22, kTagBkE2 = 0x23,
+    kTagKsA = 0x30, kTagKsE = 0x31, kTagEncA = 0x40, kTagEncE = 0x41
+};
+
+// ------------------------------------------------------------ host Goldilocks NTT
+constexpr uint64_t P = kGoldilocks;
+
+inline uint64_t hadd(uint64_t a, uint64_t b) {
+    unsigned __int128 s = (unsigned __int128)a + b;
+    if (s >= P) s -= P;
+    return (uint64_t)s;
+}
+inline uint64_t hsub(uint64_t a, uint64_t b) { return a >= b ? a - b : a + (P - b); }
+inline uint64_t hmul(uint64_t a, uint64_t b) {
+    const unsigned __int128 x = (unsigned __int128)a * b;
+    const uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
+    const uint64_t eps = 0xFFFFFFFFull;  // 2^64 mod p
+    const uint64_t hh = hi >> 32, hl = hi & eps;
+    // x = lo + hl * 2^64 + hh * 2^96 = lo + hl * (2^32 - 1) - hh  (mod p)
+    uint64_t t0 = lo - hh;
+    if (lo < hh) t0 -= eps;
+    const uint64_t t1 = hl * eps;
+    uint64_t r = t0 + t1;
+    if (r < t1) r += eps;
+    return r >= P ? r - P : r;
+}
+inline uint64_t hpow(uint64_t b, uint64_t e) {
+    uint64_t r = 1;
+    while (e) {
+        if (e & 1) r = hmul(r, b);
+        b = hmul(b, b);
+        e >>= 1;
+    }
+    return r;
+}
+
+struct HostNtt {
+    uint32_t N = 0, logN = 0;
+    std::vector<uint64_t> psi_rev, psi_inv_rev;
+    uint64_t n_inv = 0;
+    bool init(uint32_t n_) {
+        N = n_;
+        logN = 0;
+        while ((1u << logN) < N) ++logN;
+        // 7 generates the multiplicative group of the Goldilocks field.
+        const uint64_t psi = hpow(7, (P - 1) / (2ull * N));
+        if (hpow(psi, N) != P - 1) return false;  // psi must be a primitive 2N-th root
+        const uint64_t psi_inv = hpow(psi, P - 2);
+        psi_rev.assign(N, 0);
+        psi_inv_rev.assign(N, 0);
+        for (uint32_t m = 0; m < N; ++m) {
+            uint32_t r = 0;
+            for (uint32_t b = 0; b < logN; ++b)
+                if (m & (1u << b)) r |= 1u << (logN - 1 - b);
+            psi_rev[m] = hpow(psi, r);
+            psi_inv_rev[m] = hpow(psi_inv, r);
+        }
+        n_inv = hpow(N, P - 2);
+        return true;
+    }
+    // Cooley-Tukey, natural order in, bit-reversed order out.
+    void forward(uint64_t *a) const {
+        uint32_t t = N;
+        for (uint32_t m = 1; m < N; m <<= 1) {
+            t >>= 1;
+            for (uint32_t i = 0; i < m; ++i) {
+                const uint32_t j1 = 2 * i * t;
+                const uint64_t S = psi_rev[m + i];
+                for (uint32_t j = j1; j < j1 + t; ++j) {
+                    const uint64_t U = a[j], V = hmul(a[j + t], S);
+                    a[j] = hadd(U, V);
+                    a[j + t] = hsub(U, V);
+                }
+            }
+        }
+    }
+    // Gentleman-Sande, bit-reversed in, natural out, including 1/N.
+    void inverse(uint64_t *a) const {
+        uint32_t t = 1;
+        for (uint32_t m = N; m > 1; m >>= 1) {
+            uint32_t j1 = 0;
+            const uint32_t h = m >> 1;
+            for (uint32_t i = 0; i < h; ++i) {
+                const uint64_t S = psi_inv_rev[h + i];
+                for (uint32_t j = j1; j < j1 + t; ++j) {
+                    const uint64_t U = a[j], V = a[j + t];
+                    a[j] = hadd(U, V);
+                    a[j + t] = hmul(hsub(U, V), S);
+                }
+                j1 += 2 * t;
+            }
+            t <<= 1;
+        }
+        for (uint32_t j = 0; j < N; ++j) a[j] = hmul(a[j], n_inv);
+    }
+    // Torus32 polynomial (coefficients taken in [0, 2^32)) to the NTT domain.
+    void to_ntt(const uint32_t *src, uint64_t *dst, bool negate, bool scale_inv_n) const {
+        for (uint32_t j = 0; j < N; ++j) dst[j] = negate ? hsub(0, src[j]) : (uint64_t)src[j];
+        forward(dst);
+        if (scale_inv_n)
+            for (uint32_t j = 0; j < N; ++j) dst[j] = hmul(dst[j], n_inv);
+    }
+    // out = binary * q (negacyclic, mod 2^32).  The integer result lies in
+    // (-N*2^32, N*2^32), far inside (-p/2, p/2): lift the field value to that
+    // integer (p = 1 mod 2^32, so a negative x maps to (uint32)(x + p) - 1).
+    void mul_binary(const uint64_t *bin_hat, const uint32_t *q, uint32_t *out, std::vector<uint64_t> &tmp) const {
+        tmp.resize(N);
+        for (uint32_t j = 0; j < N; ++j) tmp[j] = q[j];
+        forward(tmp.data());
+        for (uint32_t j = 0; j < N; ++j) tmp[j] = hmul(tmp[j], bin_hat[j]);
+        inverse(tmp.data());
+        for (uint32_t j = 0; j < N; ++j) out[j] = (uint32_t)tmp[j] - (tmp[j] > (P >> 1) ? 1u : 0u);
+    }
+};
+
+template <class F>
+void parallel_for(size_t count, F &&fn) {
+    unsigned nt = std::thread::hardware_concurrency();
+    if (nt == 0) nt = 1;
+    if (nt > 64) nt = 64;
+    if (count < 2 || nt == 1) {
+        for (size_t i = 0; i < count; ++i) fn(i);
+        return;
+    }
+    if (nt > count) nt = (unsigned)count;
+    std::vector<std::thread> th;
+    for (unsigned w = 0; w < nt; ++w)
+        th.emplace_back([&, w]() {
+            for (size_t i = w; i < count; i += nt) fn(i);
+        });
+    for (auto &x : th) x.join();
+}
+
+uint64_t fnv1a64(const unsigned char *p, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+}  // namespace
+}  // namespace mk
+
+using namespace mk;
+
+struct PartyKeys {
+    bool has_public = false, has_secret = false;
+    std::vector<uint32_t> s, z, pk, bk, ks;
+};
+
+struct mk_ctx {
+    mk_params P{};
+    uint32_t logN = 0;
+    uint64_t crs_seed = 0;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    int form = MK_FORM_NTT;
+    int variant = 1;
+    uint32_t max_batch = 4096;
+    std::vector<uint32_t> crs;
+    std::vector<PartyKeys> party;
+    HostNtt ntt;
+    // device state
+    bool dev_keys_valid = false;
+    uint64_t *d_tw = nullptr;   // [2][N]
+    uint64_t *d_bk = nullptr;   // [k][n][3][d][N]
+    uint64_t *d_keyA = nullptr; // [(k+1)][d][N]
+    uint32_t *d_ks = nullptr;   // [k][N][t][B'-1][n+1]
+    uint32_t *d_ext = nullptr;  // scratch [scratch_gates][k*N+1]
+    GateDesc *d_desc = nullptr; // scratch [scratch_gates]
+    uint32_t scratch_gates = 0;
+    std::string err;
+    // measurement: event pairs around launches, per kernel class
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
+    std::vector<cudaEvent_t> ev_pool;
+
+    size_t W() const { return (size_t)P.k * P.n + 1; }
+    size_t E() const { return (size_t)P.k * P.N + 1; }
+    size_t pk_words() const { return (size_t)P.d * P.N; }
+    size_t bk_words() const { return (size_t)P.n * 3 * P.d * P.N; }
+    size_t ks_words() const { return (size_t)P.N * P.t * ((1u << P.ks_bit) - 1) * (P.n + 1); }
+    LaunchShape shape() const { return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant}; }
+    DeviceKeys dkeys() const { return DeviceKeys{d_tw, d_tw + P.N, d_bk, d_keyA, d_ks}; }
+};
+
+namespace {
+
+int fail(mk_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(mk_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, MK_EDEVICE, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define MK_CUDA(c, expr)                                         \
+    do {                                                         \
+        cudaError_t e__ = (expr);                                \
+        if (e__ != cudaSuccess) return cuda_fail((c), e__, #expr); \
+    } while (0)
+
+bool params_supported(const mk_params &p, std::string &why) {
+    if (p.k < 1 || p.k > 8) { why = "k must be in [1, 8]"; return false; }
+    if (p.N != 256 && p.N != 1024) { why = "N must be 256 or 1024"; return false; }
+    if (p.n < 1 || p.n > 4096) { why = "n must be in [1, 4096]"; return false; }
+    if (p.d != 3) { why = "the kernels decompose with d = 3 gadget digits"; return false; }
+    if (p.bg_bit < 1 || p.bg_bit * p.d > 32 || p.bg_bit > 10) { why = "need 1 <= bg_bit <= 10 and bg_bit*d <= 32"; return false; }
+    if (p.ks_bit < 1 || p.t < 1 || p.ks_bit * p.t > 31 || p.ks_bit > 8) { why = "need ks_bit*t <= 31, ks_bit <= 8"; return false; }
+    if (!(p.sigma_lwe >= 0) || !(p.sigma_rlwe >= 0)) { why = "sigmas must be >= 0"; return false; }
+    return true;
+}
+
+cudaEvent_t take_event(mk_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void release_timing(mk_ctx *c) {
+    for (auto &v : c->ev)
+        for (auto &pr : v) {
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+    c->ev[0].clear();
+    c->ev[1].clear();
+}
+
+// Launch `fn` and, when timing is on, bracket it with events on the stream.
+template <class F>
+cudaError_t timed(mk_ctx *c, int kind, F &&fn) {
+    if (!c->timing) return fn();
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    cudaEventRecord(a, c->stream);
+    cudaError_t e = fn();
+    cudaEventRecord(b, c->stream);
+    c->ev[kind].emplace_back(a, b);
+    return e;
+}
+
+void free_device(mk_ctx *c) {
+    if (c->device < 0) return;
+    cudaSetDevice(c->device);
+    release_timing(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
+    cudaFree(c->d_tw);
+    cudaFree(c->d_bk);
+    cudaFree(c->d_keyA);
+    cudaFree(c->d_ks);
+    cudaFree(c->d_ext);
+    cudaFree(c->d_desc);
+    c->d_tw = nullptr;
+    c->d_bk = c->d_keyA = nullptr;
+    c->d_ks = c->d_ext = nullptr;
+    c->d_desc = nullptr;
+    c->scratch_gates = 0;
+    c->dev_keys_valid = false;
+}
+
+int check_party_public(mk_ctx *c) {
+    for (uint32_t i = 0; i < c->P.k; ++i)
+        if (!c->party[i].has_public) return fail(c, MK_ESTATE, "public keys of party " + std::to_string(i) + " missing");
+    return MK_OK;
+}
+
+int check_all_secret(mk_ctx *c) {
+    for (uint32_t i = 0; i < c->P.k; ++i)
+        if (!c->party[i].has_secret) return fail(c, MK_ESTATE, "secret key of party " + std::to_string(i) + " missing");
+    return MK_OK;
+}
+
+// Build the NTT-domain bootstrapping keys and upload everything the kernels read.
+int ensure_device_keys(mk_ctx *c) {
+    if (c->device < 0) return fail(c, MK_EDEVICE, "host-only context (device = -1)");
+    int rc = check_party_public(c);
+    if (rc) return rc;
+    if (c->dev_keys_valid) return MK_OK;
+    MK_CUDA(c, cudaSetDevice(c->device));
+    const uint32_t N = c->P.N, n = c->P.n, k = c->P.k, d = c->P.d;
+    const size_t bk_entries = (size_t)k * n * 3 * d;  // polynomials
+    std::vector<uint64_t> h_bk(bk_entries * N), h_keyA((size_t)(k + 1) * d * N), h_tw(2 * (size_t)N);
+    for (uint32_t m = 0; m < N; ++m) {
+        h_tw[m] = c->ntt.psi_rev[m];
+        h_tw[N + m] = c->ntt.psi_inv_rev[m];
+    }
+    parallel_for(bk_entries, [&](size_t e) {
+        const uint32_t i = (uint32_t)(e / ((size_t)n * 3 * d));
+        const size_t within = e % ((size_t)n * 3 * d);
+        c->ntt.to_ntt(c->party[i].bk.data() + within * N, h_bk.data() + e * N, false, true);
+    });
+    for (uint32_t l = 0; l < d; ++l) c->ntt.to_ntt(c->crs.data() + (size_t)l * N, h_keyA.data() + (size_t)l * N, true, true);
+    for (uint32_t j = 1; j <= k; ++j)
+        for (uint32_t l = 0; l < d; ++l)
+            c->ntt.to_ntt(c->party[j - 1].pk.data() + (size_t)l * N, h_keyA.data() + ((size_t)j * d + l) * N, false, true);
+    if (!c->d_tw) MK_CUDA(c, cudaMalloc(&c->d_tw, h_tw.size() * 8));
+    if (!c->d_bk) MK_CUDA(c, cudaMalloc(&c->d_bk, h_bk.size() * 8));
+    if (!c->d_keyA) MK_CUDA(c, cudaMalloc(&c->d_keyA, h_keyA.size() * 8));
+    if (!c->d_ks) MK_CUDA(c, cudaMalloc(&c->d_ks, (size_t)k * c->ks_words() * 4));
+    MK_CUDA(c, cudaMemcpy(c->d_tw, h_tw.data(), h_tw.size() * 8, cudaMemcpyHostToDevice));
+    MK_CUDA(c, cudaMemcpy(c->d_bk, h_bk.data(), h_bk.size() * 8, cudaMemcpyHostToDevice));
+    MK_CUDA(c, cudaMemcpy(c->d_keyA, h_keyA.data(), h_keyA.size() * 8, cudaMemcpyHostToDevice));
+    for (uint32_t i = 0; i < k; ++i)
+        MK_CUDA(c, cudaMemcpy(c->d_ks + (size_t)i * c->ks_words(), c->party[i].ks.data(), c->ks_words() * 4,
+                              cudaMemcpyHostToDevice));
+    c->dev_keys_valid = true;
+    return MK_OK;
+}
+
+int ensure_scratch(mk_ctx *c, uint32_t gates) {
+    if (gates <= c->scratch_gates) return MK_OK;
+    MK_CUDA(c, cudaSetDevice(c->device));
+    // Work already enqueued may still read the old buffers.
+    MK_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_ext);
+    cudaFree(c->d_desc);
+    c->d_ext = nullptr;
+    c->d_desc = nullptr;
+    c->scratch_gates = 0;
+    MK_CUDA(c, cudaMalloc(&c->d_ext, (size_t)gates * c->E() * 4));
+    MK_CUDA(c, cudaMalloc(&c->d_desc, (size_t)gates * sizeof(GateDesc)));
+    c->scratch_gates = gates;
+    return MK_OK;
+}
+
+int device_ready(mk_ctx *c, size_t count) {
+    int rc = ensure_device_keys(c);
+    if (rc) return rc;
+    const uint32_t chunk = (uint32_t)std::min<size_t>(count, c->max_batch);
+    rc = ensure_scratch(c, chunk ? chunk : 1);
+    if (rc) return rc;
+    MK_CUDA(c, cudaSetDevice(c->device));
+    return MK_OK;
+}
+
+enum DescKind { kDescTypes, kDescLin, kDescUniform };
+
+int run_gates(mk_ctx *c, DescKind kind, const void *src, int type, const uint32_t *d_a, const uint32_t *d_b,
+              uint32_t *d_out, size_t count) {
+    if (count == 0) return MK_OK;
+    if (!d_a || !d_b || !d_out) return fail(c, MK_EINVAL, "null ciphertext pointer");
+    if (count > 0xFFFFFFFFull / 2) return fail(c, MK_EINVAL, "count too large");
+    int rc = device_ready(c, count);
+    if (rc) return rc;
+    const LaunchShape S = c->shape();
+    const DeviceKeys K = c->dkeys();
+    for (size_t start = 0; start < count; start += c->max_batch) {
+        const uint32_t cnt = (uint32_t)std::min<size_t>(c->max_batch, count - start);
+        cudaError_t e;
+        if (kind == kDescTypes) e = launch_desc_from_types((const uint8_t *)src, c->d_desc, (uint32_t)start, cnt, c->stream);
+        else if (kind == kDescLin) e = launch_desc_from_lin((const mk_lin *)src, c->d_desc, (uint32_t)start, cnt, c->stream);
+        else e = launch_desc_uniform(type, c->d_desc, (uint32_t)start, cnt, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "descriptor kernel");
+        e = timed(c, MK_KERNEL_BOOTSTRAP,
+                  [&] { return launch_bootstrap_ntt(S, K, c->d_desc, d_a, d_b, c->d_ext, cnt, c->stream); });
+        if (e != cudaSuccess) return cuda_fail(c, e, "bootstrap kernel");
+        e = timed(c, MK_KERNEL_KEYSWITCH,
+                  [&] { return launch_keyswitch(S, K, c->d_desc, c->d_ext, d_out, cnt, c->stream); });
+        if (e != cudaSuccess) return cuda_fail(c, e, "keyswitch kernel");
+    }
+    return MK_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int mk_params_preset(int preset, uint32_t k, mk_params *out) {
+    if (!out || k == 0) return MK_EINVAL;
+    mk_params p{};
+    p.k = k;
+    p.bg_bit = 8;
+    p.d = 3;
+    p.ks_bit = 2;
+    p.t = 8;
+    if (preset == MK_PRESET_TOY) {
+        p.n = 64;
+        p.N = 256;
+        p.sigma_lwe = std::ldexp(1.0, -25);
+        p.sigma_rlwe = std::ldexp(1.0, -25);
+    } else if (preset == MK_PRESET_FULL) {
+        p.n = 560;
+        p.N = 1024;
+        p.sigma_lwe = std::ldexp(1.0, -15);
+        p.sigma_rlwe = std::ldexp(1.0, k == 1 ? -28 : (k <= 3 ? -30 : -32));
+    } else if (preset == MK_PRESET_PAPER) {
+        p.n = 560;
+        p.N = 1024;
+        p.bg_bit = 9;
+        p.sigma_lwe = 3.05e-5;
+        p.sigma_rlwe = 3.72e-9;
+    } else {
+        return MK_EINVAL;
+    }
+    *out = p;
+    return MK_OK;
+}
+
+int mk_ctx_create(const mk_params *params, uint64_t crs_seed, int device, void *stream, mk_ctx **out) {
+    if (!params || !out) return MK_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (!params_supported(*params, why)) return MK_EPARAMS;
+    mk_ctx *c = new (std::nothrow) mk_ctx();
+    if (!c) return MK_ENOMEM;
+    c->P = *params;
+    c->P.reserved = 0;
+    while ((1u << c->logN) < c->P.N) ++c->logN;
+    c->crs_seed = crs_seed;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (!c->ntt.init(c->P.N)) {
+        delete c;
+        return MK_EPARAMS;
+    }
+    c->party.resize(c->P.k);
+    // Setup: the common reference string a in T_N[X]^d.
+    const uint32_t N = c->P.N, d = c->P.d;
+    c->crs.resize((size_t)d * N);
+    Philox crs_rng(crs_seed, kTagCrs);
+    for (size_t q = 0; q < c->crs.size(); ++q) c->crs[q] = crs_rng.word(q);
+    if (device >= 0) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
+            delete c;
+            return MK_EDEVICE;
+        }
+        if (cudaSetDevice(device) != cudaSuccess) {
+            delete c;
+            return MK_EDEVICE;
+        }
+    }
+    *out = c;
+    return MK_OK;
+}
+
+int mk_ctx_destroy(mk_ctx *c) {
+    if (!c) return MK_EINVAL;
+    if (c->device >= 0) {
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
+    }
+    free_device(c);
+    delete c;
+    return MK_OK;
+}
+
+int mk_ctx_set_stream(mk_ctx *c, void *stream) {
+    if (!c) return MK_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return MK_OK;
+}
+
+int mk_ctx_get_params(const mk_ctx *c, mk_params *out) {
+    if (!c || !out) return MK_EINVAL;
+    *out = c->P;
+    return MK_OK;
+}
+
+int mk_ctx_set_form(mk_ctx *c, int form) {
+    if (!c) return MK_EINVAL;
+    if (form != MK_FORM_NTT) return fail(c, MK_EINVAL, "unknown product form");
+    c->form = form;
+    return MK_OK;
+}
+
+int mk_ctx_set_batch(mk_ctx *c, uint32_t max_gates) {
+    if (!c || max_gates == 0 || max_gates > (1u << 20)) return c ? fail(c, MK_EINVAL, "batch must be in [1, 2^20]") : MK_EINVAL;
+    c->max_batch = max_gates;
+    return MK_OK;
+}
+
+int mk_ctx_set_variant(mk_ctx *c, int v) {
+    if (!c) return MK_EINVAL;
+    if (v < 0 || v >= kNumVariants) return fail(c, MK_EINVAL, "variant out of range");
+    c->variant = v;
+    return MK_OK;
+}
+
+int mk_ctx_get_variant(const mk_ctx *c, int *v) {
+    if (!c || !v) return MK_EINVAL;
+    *v = c->variant;
+    return MK_OK;
+}
+
+int mk_autotune(mk_ctx *c, uint32_t sample_gates, int *best, float *ms_out) {
+    if (!c || sample_gates == 0) return MK_EINVAL;
+    int rc = device_ready(c, sample_gates);
+    if (rc) return rc;
+    const size_t W = c->W();
+    const uint32_t cnt = std::min<uint32_t>(sample_gates, c->max_batch);
+    // Random ciphertexts: every CMux step is active, as for real multi-party inputs.
+    std::vector<uint32_t> h((size_t)2 * cnt * W);
+    const Philox r(0xA5A5A5A5ull, 0x7F);
+    for (size_t q = 0; q < h.size(); ++q) h[q] = r.word(q);
+    uint32_t *d_in = nullptr, *d_out = nullptr;
+    MK_CUDA(c, cudaMalloc(&d_in, h.size() * 4));
+    if (cudaMalloc(&d_out, (size_t)cnt * W * 4) != cudaSuccess) {
+        cudaFree(d_in);
+        return fail(c, MK_ENOMEM, "autotune scratch");
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int bestv = c->variant;
+    float bestms = 1e30f;
+    cudaError_t err = cudaMemcpyAsync(d_in, h.data(), h.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    const int saved = c->variant;
+    for (int v = 0; v < kNumVariants && err == cudaSuccess; ++v) {
+        c->variant = v;
+        err = launch_desc_uniform(MK_NAND, c->d_desc, 0, cnt, c->stream);
+        if (err == cudaSuccess)
+            err = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_in, d_in + (size_t)cnt * W, c->d_ext, cnt,
+                                       c->stream);
+        cudaEventRecord(a, c->stream);
+        if (err == cudaSuccess)
+            err = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_in, d_in + (size_t)cnt * W, c->d_ext, cnt,
+                                       c->stream);
+        cudaEventRecord(b, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(b);
+        float ms = 0;
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+        if (ms_out) ms_out[v] = ms;
+        if (err == cudaSuccess && ms < bestms) {
+            bestms = ms;
+            bestv = v;
+        }
+    }
+    c->variant = (err == cudaSuccess) ? bestv : saved;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(d_in);
+    cudaFree(d_out);
+    if (err != cudaSuccess) return cuda_fail(c, err, "autotune");
+    if (best) *best = c->variant;
+    return MK_OK;
+}
+
+const char *mk_last_error(const mk_ctx *c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int mk_sync(mk_ctx *c) {
+    if (!c) return MK_EINVAL;
+    if (c->device < 0) return MK_OK;
+    MK_CUDA(c, cudaSetDevice(c->device));
+    MK_CUDA(c, cudaStreamSynchronize(c->stream));
+    MK_CUDA(c, cudaGetLastError());
+    return MK_OK;
+}
+
+// ------------------------------------------------------------------- keys
+int mk_keygen(mk_ctx *c, uint32_t party, uint64_t seed) {
+    if (!c) return MK_EINVAL;
+    if (party >= c->P.k) return fail(c, MK_EINVAL, "party index out of range");
+    const uint32_t n = c->P.n, N = c->P.N, d = c->P.d, t = c->P.t;
+    const uint32_t nb = (1u << c->P.ks_bit) - 1;
+    PartyKeys K;
+    K.s.resize(n);
+    K.z.resize(N);
+    K.pk.resize((size_t)d * N);
+    K.bk.resize(c->bk_words());
+    K.ks.resize(c->ks_words());
+    const Philox rs(seed, kTagS), rz(seed, kTagZ), rpe(seed, kTagPkE);
+    for (uint32_t j = 0; j < n; ++j) K.s[j] = rs.word(j) & 1u;
+    for (uint32_t m = 0; m < N; ++m) K.z[m] = rz.word(m) & 1u;
+    const HostNtt &T = c->ntt;
+    std::vector<uint64_t> z_hat(N);
+    for (uint32_t m = 0; m < N; ++m) z_hat[m] = K.z[m];
+    T.forward(z_hat.data());
+    {
+        std::vector<uint64_t> tmp;
+        std::vector<uint32_t> prod(N);
+        for (uint32_t l = 0; l < d; ++l) {
+            T.mul_binary(z_hat.data(), c->crs.data() + (size_t)l * N, prod.data(), tmp);
+            for (uint32_t m = 0; m < N; ++m)
+                K.pk[(size_t)l * N + m] = (0u - prod[m]) + rpe.gauss32((uint64_t)l * N + m, c->P.sigma_rlwe);
+        }
+    }
+    // BK_j = UniEnc(s_j; z): r binary, d_l = r*a_l + s_j*g_l + e1, f1_l uniform, f0_l = -z*f1_l + r*g_l + e2.
+    const Philox rr(seed, kTagBkR), rf1(seed, kTagBkF1), re1(seed, kTagBkE1), re2(seed, kTagBkE2);
+    parallel_for(n, [&](size_t jj) {
+        const uint32_t j = (uint32_t)jj;
+        std::vector<uint64_t> r_hat(N), tmp;
+        std::vector<uint32_t> r(N), prod(N);
+        for (uint32_t m = 0; m < N; ++m) {
+            r[m] = rr.word((uint64_t)j * N + m) & 1u;
+            r_hat[m] = r[m];
+        }
+        T.forward(r_hat.data());
+        uint32_t *ent = K.bk.data() + (size_t)j * 3 * d * N;
+        for (uint32_t l = 0; l < d; ++l) {
+            const uint64_t qb = ((uint64_t)j * d + l) * N;
+            const uint32_t g = 1u << (32 - c->P.bg_bit * (l + 1));
+            uint32_t *dv = ent + (size_t)l * N, *f0 = ent + (size_t)(d + l) * N, *f1 = ent + (size_t)(2 * d + l) * N;
+            T.mul_binary(r_hat.data(), c->crs.data() + (size_t)l * N, prod.data(), tmp);
+            for (uint32_t m = 0; m < N; ++m) dv[m] = prod[m] + re1.gauss32(qb + m, c->P.sigma_rlwe);
+            dv[0] += K.s[j] * g;
+            for (uint32_t m = 0; m < N; ++m) f1[m] = rf1.word(qb + m);
+            T.mul_binary(z_hat.data(), f1, prod.data(), tmp);
+            for (uint32_t m = 0; m < N; ++m) f0[m] = (0u - prod[m]) + r[m] * g + re2.gauss32(qb + m, c->P.sigma_rlwe);
+        }
+    });
+    // KS[j][l][delta-1] = LWE_s(delta * z_j * 2^(32 - ks_bit*(l+1))).
+    const Philox rka(seed, kTagKsA), rke(seed, kTagKsE);
+    const size_t rows = (size_t)N * t * nb;
+    parallel_for((rows + 255) / 256, [&](size_t blk) {
+        for (size_t row = blk * 256; row < std::min(rows, (blk + 1) * 256); ++row) {
+            const uint32_t delta = (uint32_t)(row % nb) + 1;
+            const uint32_t l = (uint32_t)((row / nb) % t);
+            const uint32_t j = (uint32_t)(row / ((size_t)nb * t));
+            uint32_t *dst = K.ks.data() + row * (n + 1);
+            uint32_t dot = 0;
+            for (uint32_t x = 0; x < n; ++x) {
+                dst[x] = rka.word((uint64_t)row * n + x);
+                dot += dst[x] * K.s[x];
+            }
+            dst[n] = (0u - dot) + delta * K.z[j] * (1u << (32 - c->P.ks_bit * (l + 1))) + rke.gauss32(row, c->P.sigma_lwe);
+        }
+    });
+    K.has_public = K.has_secret = true;
+    c->party[party] = std::move(K);
+    c->dev_keys_valid = false;
+    return MK_OK;
+}
+
+int mk_import_crs(mk_ctx *c, const uint32_t *h_crs) {
+    if (!c || !h_crs) return MK_EINVAL;
+    std::memcpy(c->crs.data(), h_crs, c->crs.size() * 4);
+    c->dev_keys_valid = false;
+    return MK_OK;
+}
+
+int mk_import_party(mk_ctx *c, uint32_t party, const uint32_t *s, const uint32_t *z, const uint32_t *pk,
+                    const uint32_t *bk, const uint32_t *ks) {
+    if (!c) return MK_EINVAL;
+    if (party >= c->P.k) return fail(c, MK_EINVAL, "party index out of range");
+    if (!pk || !bk || !ks) return fail(c, MK_EINVAL, "public key pointers must not be null");
+    if ((s == nullptr) != (z == nullptr)) return fail(c, MK_EINVAL, "give both secrets or neither");
+    PartyKeys K;
+    K.pk.assign(pk, pk + c->pk_words());
+    K.bk.assign(bk, bk + c->bk_words());
+    K.ks.assign(ks, ks + c->ks_words());
+    K.has_public = true;
+    if (s) {
+        K.s.assign(s, s + c->P.n);
+        K.z.assign(z, z + c->P.N);
+        K.has_secret = true;
+    }
+    c->party[party] = std::move(K);
+    c->dev_keys_valid = false;
+    return MK_OK;
+}
+
+int mk_export_crs(const mk_ctx *c, uint32_t *h_crs) {
+    if (!c || !h_crs) return MK_EINVAL;
+    std::memcpy(h_crs, c->crs.data(), c->crs.size() * 4);
+    return MK_OK;
+}
+
+int mk_export_party(const mk_ctx *cc, uint32_t party, uint32_t *s, uint32_t *z, uint32_t *pk, uint32_t *bk,
+                    uint32_t *ks) {
+    mk_ctx *c = const_cast<mk_ctx *>(cc);
+    if (!c) return MK_EINVAL;
+    if (party >= c->P.k) return fail(c, MK_EINVAL, "party index out of range");
+    const PartyKeys &K = c->party[party];
+    if ((pk || bk || ks) && !K.has_public) return fail(c, MK_ESTATE, "no public keys for this party");
+    if ((s || z) && !K.has_secret) return fail(c, MK_ESTATE, "no secret keys for this party");
+    if (s) std::memcpy(s, K.s.data(), K.s.size() * 4);
+    if (z) std::memcpy(z, K.z.data(), K.z.size() * 4);
+    if (pk) std::memcpy(pk, K.pk.data(), K.pk.size() * 4);
+    if (bk) std::memcpy(bk, K.bk.data(), K.bk.size() * 4);
+    if (ks) std::memcpy(ks, K.ks.data(), K.ks.size() * 4);
+    return MK_OK;
+}
+
+namespace {
+struct BlobHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    mk_params params;
+    uint64_t crs_seed;
+    uint32_t party_mask, secret_mask;
+    uint64_t payload_words;
+};
+const char kMagic[8] = {'M', 'K', 'T', 'F', 'H', 'E', 'K', '1'};
+}  // namespace
+
+int mk_save_keys(const mk_ctx *cc, int include_secrets, void *h_blob, size_t cap, size_t *len) {
+    mk_ctx *c = const_cast<mk_ctx *>(cc);
+    if (!c || !len) return MK_EINVAL;
+    BlobHeader H{};
+    std::memcpy(H.magic, kMagic, 8);
+    H.version = 1;
+    H.header_bytes = sizeof(BlobHeader);
+    H.params = c->P;
+    H.crs_seed = c->crs_seed;
+    size_t words = c->crs.size();
+    for (uint32_t i = 0; i < c->P.k; ++i) {
+        const PartyKeys &K = c->party[i];
+        if (!K.has_public) continue;
+        H.party_mask |= 1u << i;
+        words += c->pk_words() + c->bk_words() + c->ks_words();
+        if (include_secrets && K.has_secret) {
+            H.secret_mask |= 1u << i;
+            words += c->P.n + c->P.N;
+        }
+    }
+    H.payload_words = words;
+    const size_t total = sizeof(BlobHeader) + words * 4 + 8;
+    *len = total;
+    if (!h_blob) return MK_OK;
+    if (cap < total) return fail(c, MK_EINVAL, "blob buffer too small");
+    unsigned char *p = (unsigned char *)h_blob;
+    std::memcpy(p, &H, sizeof(H));
+    size_t off = sizeof(H);
+    auto put = [&](const std::vector<uint32_t> &v) {
+        std::memcpy(p + off, v.data(), v.size() * 4);
+        off += v.size() * 4;
+    };
+    put(c->crs);
+    for (uint32_t i = 0; i < c->P.k; ++i) {
+        const PartyKeys &K = c->party[i];
+        if (!(H.party_mask >> i & 1)) continue;
+        if (H.secret_mask >> i & 1) {
+            put(K.s);
+            put(K.z);
+        }
+        put(K.pk);
+        put(K.bk);
+        put(K.ks);
+    }
+    const uint64_t h = fnv1a64(p, off);
+    std::memcpy(p + off, &h, 8);
+    return MK_OK;
+}
+
+int mk_load_keys(mk_ctx *c, const void *h_blob, size_t len) {
+    if (!c || !h_blob) return MK_EINVAL;
+    if (len < sizeof(BlobHeader) + 8) return fail(c, MK_EFORMAT, "blob too short");
+    BlobHeader H;
+    std::memcpy(&H, h_blob, sizeof(H));
+    if (std::memcmp(H.magic, kMagic, 8) != 0 || H.version != 1 || H.header_bytes != sizeof(BlobHeader))
+        return fail(c, MK_EFORMAT, "bad blob header");
+    mk_params a = H.params, b = c->P;
+    a.reserved = b.reserved = 0;
+    if (std::memcmp(&a, &b, sizeof(mk_params)) != 0) return fail(c, MK_EFORMAT, "blob parameters differ from the context's");
+    if (sizeof(BlobHeader) + H.payload_words * 4 + 8 != len) return fail(c, MK_EFORMAT, "blob size mismatch");
+    const unsigned char *p = (const unsigned char *)h_blob;
+    uint64_t stored;
+    std::memcpy(&stored, p + len - 8, 8);
+    if (fnv1a64(p, len - 8) != stored) return fail(c, MK_EFORMAT, "blob checksum mismatch");
+    size_t expect = c->crs.size();
+    for (uint32_t i = 0; i < c->P.k; ++i) {
+        if (H.party_mask >> i & 1) expect += c->pk_words() + c->bk_words() + c->ks_words();
+        if (H.secret_mask >> i & 1) {
+            if (!(H.party_mask >> i & 1)) return fail(c, MK_EFORMAT, "secret without public keys");
+            expect += c->P.n + c->P.N;
+        }
+    }
+    if (expect != H.payload_words || (H.party_mask >> c->P.k) != 0) return fail(c, MK_EFORMAT, "blob party layout mismatch");
+    size_t off = sizeof(H);
+    auto get = [&](std::vector<uint32_t> &v, size_t words) {
+        v.resize(words);
+        std::memcpy(v.data(), p + off, words * 4);
+        off += words * 4;
+    };
+    std::vector<uint32_t> crs;
+    get(crs, c->crs.size());
+    std::vector<PartyKeys> parties(c->P.k);
+    for (uint32_t i = 0; i < c->P.k; ++i) {
+        PartyKeys &K = parties[i];
+        if (!(H.party_mask >> i & 1)) continue;
+        if (H.secret_mask >> i & 1) {
+            get(K.s, c->P.n);
+            get(K.z, c->P.N);
+            K.has_secret = true;
+        }
+        get(K.pk, c->pk_words());
+        get(K.bk, c->bk_words());
+        get(K.ks, c->ks_words());
+        K.has_public = true;
+    }
+    c->crs = std::move(crs);
+    for (uint32_t i = 0; i < c->P.k; ++i)
+        if (parties[i].has_public) c->party[i] = std::move(parties[i]);
+    c->crs_seed = H.crs_seed;
+    c->dev_keys_valid = false;
+    return MK_OK;
+}
+
+// ------------------------------------------------------------------- enc / dec
+int mk_encrypt(mk_ctx *c, uint32_t party, const uint8_t *bits, size_t count, uint64_t seed, uint32_t *ct) {
+    if (!c) return MK_EINVAL;
+    if (party >= c->P.k) return fail(c, MK_EINVAL, "party index out of range");
+    if (count && (!bits || !ct)) return fail(c, MK_EINVAL, "null pointer");
+    if (!c->party[party].has_secret) return fail(c, MK_ESTATE, "secret key of this party missing");
+    const uint32_t n = c->P.n, k = c->P.k;
+    const size_t W = c->W();
+    const std::vector<uint32_t> &s = c->party[party].s;
+    const Philox ra(seed, kTagEncA), re(seed, kTagEncE);
+    parallel_for((count + 63) / 64, [&](size_t blk) {
+        for (size_t g = blk * 64; g < std::min(count, (blk + 1) * 64); ++g) {
+            uint32_t *row = ct + g * W;
+            std::memset(row, 0, W * 4);
+            uint32_t dot = 0;
+            for (uint32_t x = 0; x < n; ++x) {
+                const uint32_t a = ra.word((uint64_t)g * n + x);
+                row[(size_t)party * n + x] = a;
+                dot += a * s[x];
+            }
+            row[(size_t)k * n] = (0u - dot) + ((bits[g] & 1u) ? (1u << 30) : 0u) + re.gauss32(g, c->P.sigma_lwe);
+        }
+    });
+    return MK_OK;
+}
+
+int mk_encrypt_joint(mk_ctx *c, const uint8_t *bits, size_t count, uint64_t seed, uint32_t *ct) {
+    if (!c) return MK_EINVAL;
+    if (count && (!bits || !ct)) return fail(c, MK_EINVAL, "null pointer");
+    int rc = check_all_secret(c);
+    if (rc) return rc;
+    const uint32_t n = c->P.n, k = c->P.k;
+    const size_t W = c->W();
+    const Philox ra(seed, kTagEncA), re(seed, kTagEncE);
+    parallel_for((count + 63) / 64, [&](size_t blk) {
+        for (size_t g = blk * 64; g < std::min(count, (blk + 1) * 64); ++g) {
+            uint32_t *row = ct + g * W;
+            uint32_t dot = 0;
+            for (size_t x = 0; x < (size_t)k * n; ++x) {
+                const uint32_t a = ra.word((uint64_t)g * k * n + x);
+                row[x] = a;
+                dot += a * c->party[x / n].s[x % n];
+            }
+            row[(size_t)k * n] = (0u - dot) + ((bits[g] & 1u) ? (1u << 30) : 0u) + re.gauss32(g, c->P.sigma_lwe);
+        }
+    });
+    return MK_OK;
+}
+
+static int get_host_rows(mk_ctx *c, const uint32_t *ct, size_t count, int on_device, std::vector<uint32_t> &buf,
+                         const uint32_t **rows) {
+    if (!on_device) {
+        *rows = ct;
+        return MK_OK;
+    }
+    if (c->device < 0) return fail(c, MK_EDEVICE, "host-only context");
+    buf.resize(count * c->W());
+    MK_CUDA(c, cudaSetDevice(c->device));
+    MK_CUDA(c, cudaMemcpyAsync(buf.data(), ct, buf.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    MK_CUDA(c, cudaStreamSynchronize(c->stream));
+    *rows = buf.data();
+    return MK_OK;
+}
+
+int mk_phase(mk_ctx *c, const uint32_t *ct, size_t count, int on_device, uint32_t *phase) {
+    if (!c) return MK_EINVAL;
+    if (count && (!ct || !phase)) return fail(c, MK_EINVAL, "null pointer");
+    int rc = check_all_secret(c);
+    if (rc) return rc;
+    std::vector<uint32_t> buf;
+    const uint32_t *rows = nullptr;
+    rc = get_host_rows(c, ct, count, on_device, buf, &rows);
+    if (rc) return rc;
+    const uint32_t n = c->P.n, k = c->P.k;
+    const size_t W = c->W();
+    for (size_t g = 0; g < count; ++g) {
+        const uint32_t *row = rows + g * W;
+        uint32_t ph = row[(size_t)k * n];
+        for (uint32_t i = 0; i < k; ++i) {
+            const uint32_t *s = c->party[i].s.data();
+            for (uint32_t x = 0; x < n; ++x) ph += row[(size_t)i * n + x] * s[x];
+        }
+        phase[g] = ph;
+    }
+    return MK_OK;
+}
+
+int mk_decrypt(mk_ctx *c, const uint32_t *ct, size_t count, int on_device, uint8_t *bits) {
+    if (!c) return MK_EINVAL;
+    if (count && !bits) return fail(c, MK_EINVAL, "null pointer");
+    std::vector<uint32_t> ph(count);
+    int rc = mk_phase(c, ct, count, on_device, ph.data());
+    if (rc) return rc;
+    // m = 1 iff the phase lies in [1/8, 5/8): the nearer of 0 and 1/4.
+    for (size_t g = 0; g < count; ++g) bits[g] = (uint8_t)((uint32_t)(ph[g] - (1u << 29)) < (1u << 31));
+    return MK_OK;
+}
+
+// ------------------------------------------------------------------- gates
+int mk_gate(mk_ctx *c, int type, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out, size_t count) {
+    if (!c) return MK_EINVAL;
+    if (type < MK_AND || type > MK_XNOR) return fail(c, MK_EINVAL, "unknown gate type");
+    return run_gates(c, kDescUniform, nullptr, type, d_a, d_b, d_out, count);
+}
+
+int mk_gates(mk_ctx *c, const uint8_t *d_types, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+             size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count && !d_types) return fail(c, MK_EINVAL, "null type pointer");
+    return run_gates(c, kDescTypes, d_types, 0, d_a, d_b, d_out, count);
+}
+
+int mk_gates_lin(mk_ctx *c, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+                 size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count && !d_lin) return fail(c, MK_EINVAL, "null mk_lin pointer");
+    return run_gates(c, kDescLin, d_lin, 0, d_a, d_b, d_out, count);
+}
+
+int mk_not(mk_ctx *c, const uint32_t *d_a, uint32_t *d_out, size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count == 0) return MK_OK;
+    if (!d_a || !d_out) return fail(c, MK_EINVAL, "null pointer");
+    if (c->device < 0) return fail(c, MK_EDEVICE, "host-only context");
+    MK_CUDA(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_not(c->shape(), d_a, d_out, count, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "not kernel");
+    return MK_OK;
+}
+
+// ------------------------------------------------------------------- stages
+int mk_stage_modswitch(mk_ctx *c, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_abar,
+                       size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count == 0) return MK_OK;
+    if (!d_lin || !d_a || !d_b || !d_abar) return fail(c, MK_EINVAL, "null pointer");
+    int rc = device_ready(c, count);
+    if (rc) return rc;
+    for (size_t start = 0; start < count; start += c->max_batch) {
+        const uint32_t cnt = (uint32_t)std::min<size_t>(c->max_batch, count - start);
+        cudaError_t e = launch_desc_from_lin(d_lin, c->d_desc, (uint32_t)start, cnt, c->stream);
+        if (e == cudaSuccess)
+            e = launch_modswitch(c->shape(), c->d_desc, d_a, d_b, d_abar + start * c->W(), cnt, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "modswitch");
+    }
+    return MK_OK;
+}
+
+int mk_stage_blind_rotate(mk_ctx *c, const uint32_t *d_abar, size_t count, int64_t max_steps, uint32_t *d_acc) {
+    if (!c) return MK_EINVAL;
+    if (count == 0) return MK_OK;
+    if (!d_abar || !d_acc) return fail(c, MK_EINVAL, "null pointer");
+    if (count > 0xFFFFFFFFull) return fail(c, MK_EINVAL, "count too large");
+    int rc = device_ready(c, 1);
+    if (rc) return rc;
+    cudaError_t e = launch_blind_rotate_ntt(c->shape(), c->dkeys(), d_abar, (uint32_t)count, max_steps, d_acc, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "blind rotation");
+    return MK_OK;
+}
+
+int mk_stage_bootstrap(mk_ctx *c, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_ext,
+                       size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count == 0) return MK_OK;
+    if (!d_lin || !d_a || !d_b || !d_ext) return fail(c, MK_EINVAL, "null pointer");
+    int rc = device_ready(c, count);
+    if (rc) return rc;
+    for (size_t start = 0; start < count; start += c->max_batch) {
+        const uint32_t cnt = (uint32_t)std::min<size_t>(c->max_batch, count - start);
+        cudaError_t e = launch_desc_from_lin(d_lin, c->d_desc, (uint32_t)start, cnt, c->stream);
+        if (e == cudaSuccess)
+            e = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_a, d_b, d_ext + start * c->E(), cnt,
+                                     c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "bootstrap");
+    }
+    return MK_OK;
+}
+
+int mk_stage_keyswitch(mk_ctx *c, const uint32_t *d_ext, uint32_t *d_out, size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count == 0) return MK_OK;
+    if (!d_ext || !d_out) return fail(c, MK_EINVAL, "null pointer");
+    if (count > 0xFFFFFFFFull) return fail(c, MK_EINVAL, "count too large");
+    int rc = device_ready(c, 1);
+    if (rc) return rc;
+    cudaError_t e = launch_keyswitch(c->shape(), c->dkeys(), nullptr, d_ext, d_out, (uint32_t)count, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "keyswitch");
+    return MK_OK;
+}
+
+// ------------------------------------------------------------------- measurement
+int mk_timing_enable(mk_ctx *c, int on) {
+    if (!c) return MK_EINVAL;
+    if (c->device < 0) return fail(c, MK_EDEVICE, "host-only context");
+    c->timing = on != 0;
+    return MK_OK;
+}
+
+int mk_timing_reset(mk_ctx *c) {
+    if (!c) return MK_EINVAL;
+    if (c->device < 0) return MK_OK;
+    MK_CUDA(c, cudaSetDevice(c->device));
+    MK_CUDA(c, cudaStreamSynchronize(c->stream));
+    release_timing(c);
+    return MK_OK;
+}
+
+int mk_timing_read(mk_ctx *c, int kernel, double *ms_total, uint64_t *launches) {
+    if (!c || !ms_total || !launches || kernel < 0 || kernel > 1) return MK_EINVAL;
+    *ms_total = 0;
+    *launches = c->ev[kernel].size();
+    if (c->device < 0) return MK_OK;
+    MK_CUDA(c, cudaSetDevice(c->device));
+    MK_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto &pr : c->ev[kernel]) {
+        float ms = 0;
+        MK_CUDA(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+        *ms_total += ms;
+    }
+    return MK_OK;
+}
+
+int mk_measure_butterfly_rate(int device, void *stream, uint32_t iters, double *per_s) {
+    if (!per_s || iters == 0) return MK_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return MK_EDEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MK_EDEVICE;
+    const uint32_t threads = 256, blocks = (uint32_t)prop.multiProcessorCount * 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t *sink = nullptr;
+    if (cudaMalloc(&sink, blocks * sizeof(uint64_t)) != cudaSuccess) return MK_ENOMEM;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int rc = MK_OK;
+    if (launch_butterfly_peak(blocks, threads, iters / 8 + 1, sink, st) != cudaSuccess) rc = MK_EDEVICE;  // warm-up
+    cudaEventRecord(a, st);
+    if (launch_butterfly_peak(blocks, threads, iters, sink, st) != cudaSuccess) rc = MK_EDEVICE;
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) rc = MK_EDEVICE;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    *per_s = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return rc;
+}
+
+}  // extern "C"

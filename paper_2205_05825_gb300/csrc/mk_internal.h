@@ -1,0 +1,100 @@
+// Internal interface between the host runtime (mk_host.cpp) and the CUDA
+// kernels (mk_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/mk_tfhe.h"
+
+namespace mk {
+
+// Goldilocks prime 2^64 - 2^32 + 1: the NTT modulus of the exact product form.
+constexpr uint64_t kGoldilocks = 0xFFFFFFFF00000001ull;
+
+// Per-gate record consumed by the fused linear + blind-rotation kernel.
+struct GateDesc {
+    uint32_t ia, ib;   // row indices into the a / b ciphertext arrays
+    uint32_t cst;      // torus constant of the linear part
+    int32_t s1, s2;    // integer scalars of the linear part
+    uint32_t out;      // row index of the output ciphertext
+};
+
+// Device-resident key material of one context, in the layouts the kernels read.
+struct DeviceKeys {
+    const uint64_t *tw_fwd;  // [N] psi^bitrev(m), Goldilocks
+    const uint64_t *tw_inv;  // [N] psi^-bitrev(m)
+    const uint64_t *bk;      // [k][n][3][d][N] NTT domain, bit-reversed order, times N^-1
+    const uint64_t *keyA;    // [(k+1)][d][N]: [0] = NTT(-a), [j] = NTT(pk_j), times N^-1
+    const uint32_t *ks;      // [k][N][t][B'-1][n+1] torus32
+};
+
+struct LaunchShape {
+    uint32_t n, N, logN, k, d, bg_bit, ks_bit, t;
+    int variant;  // blind-rotation variant (see kVariantNpf)
+};
+
+// a1-a8: linear part, window shift, modulus switch, blind rotation (NTT form),
+// SampleExtract, +1/8.  ext: [count][k*N + 1].  If abar_out != nullptr the
+// kernel stops after the modulus switch and writes it there instead.
+cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
+                                 const uint32_t *ct_a, const uint32_t *ct_b, uint32_t *ext,
+                                 uint32_t count, cudaStream_t st);
+
+// Mod switch only (stage output).
+cudaError_t launch_modswitch(const LaunchShape &S, const GateDesc *desc, const uint32_t *ct_a,
+                             const uint32_t *ct_b, uint32_t *abar, uint32_t count, cudaStream_t st);
+
+// Blind rotation from precomputed abar with a step limit (stage output).
+cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, const uint32_t *abar,
+                                    uint32_t count, int64_t max_steps, uint32_t *acc,
+                                    cudaStream_t st);
+
+// Blind-rotation variants: digit polynomials per forward transform (1 or 3)
+// and the minimum resident CTAs per SM the register allocation is capped for.
+constexpr int kNumVariants = 4;
+constexpr int kVariantNpf[kNumVariants] = {3, 3, 1, 1};
+constexpr int kVariantMinBlocks[kNumVariants] = {1, 2, 3, 4};
+
+// Per-(ring dimension, variant) blind-rotation launchers, one translation unit
+// each (mk_br.cu built with -DMK_LOGN -DMK_VARIANT).  abar_in == nullptr: the
+// gate's linear part and modulus switch come from desc/ct_a/ct_b;
+// acc_out == nullptr: the extracted LWE goes to ext, otherwise the raw
+// accumulator to acc_out.
+#define MK_DECLARE_BOOTSTRAP(LOGN, V)                                                                         \
+    cudaError_t launch_bootstrap_logn##LOGN##_v##V(const LaunchShape &S, const DeviceKeys &K,                 \
+                                                   const GateDesc *desc, const uint32_t *ct_a,                \
+                                                   const uint32_t *ct_b, const uint32_t *abar_in,             \
+                                                   int64_t max_steps, uint32_t *ext, uint32_t *acc_out,       \
+                                                   uint32_t count, cudaStream_t st);
+MK_DECLARE_BOOTSTRAP(8, 0)
+MK_DECLARE_BOOTSTRAP(8, 1)
+MK_DECLARE_BOOTSTRAP(8, 2)
+MK_DECLARE_BOOTSTRAP(8, 3)
+MK_DECLARE_BOOTSTRAP(10, 0)
+MK_DECLARE_BOOTSTRAP(10, 1)
+MK_DECLARE_BOOTSTRAP(10, 2)
+MK_DECLARE_BOOTSTRAP(10, 3)
+
+// a9: per-party key switch of ext [count][k*N+1] into out rows desc[g].out
+// (or row g when desc == nullptr).
+cudaError_t launch_keyswitch(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
+                             const uint32_t *ext, uint32_t *out, uint32_t count, cudaStream_t st);
+
+// Eq. 8: out = (0, 1/4) - in.
+cudaError_t launch_not(const LaunchShape &S, const uint32_t *in, uint32_t *out, size_t count,
+                       cudaStream_t st);
+
+// Build GateDesc records on the device from gate types (uint8) or mk_lin.
+cudaError_t launch_desc_from_types(const uint8_t *types, GateDesc *desc, uint32_t base,
+                                   uint32_t count, cudaStream_t st);
+cudaError_t launch_desc_from_lin(const mk_lin *lin, GateDesc *desc, uint32_t base, uint32_t count,
+                                 cudaStream_t st);
+cudaError_t launch_desc_uniform(int type, GateDesc *desc, uint32_t base, uint32_t count, cudaStream_t st);
+
+// Register-resident Goldilocks butterfly loop (ALU ceiling measurement).
+// Each thread performs iters * 8 butterflies; sink receives one word per block.
+cudaError_t launch_butterfly_peak(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *sink,
+                                  cudaStream_t st);
+
+}  // namespace mk

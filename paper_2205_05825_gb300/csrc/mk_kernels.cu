@@ -1,0 +1,230 @@
+// mk_kernels.cu -- sm_103a kernels of multi-key TFHE gates other than the
+// blind rotation (which lives in mk_bootstrap.cuh): modulus switch stage,
+// MKKeySwitch (Sec. 2.2 of arXiv 2205.05825), MKNOT (Eq. 8), gate
+// descriptors, and the dispatch to the per-ring-dimension blind rotation.
+#include "mk_internal.h"
+
+namespace mk {
+namespace {
+
+__global__ void modswitch_kernel(LaunchShape S, const GateDesc *__restrict__ desc, const uint32_t *__restrict__ ct_a,
+                                 const uint32_t *__restrict__ ct_b, uint32_t *__restrict__ abar_out) {
+    const uint32_t W = S.k * S.n + 1;
+    const uint32_t sh = 32 - (S.logN + 1);
+    const GateDesc g = desc[blockIdx.x];
+    const uint32_t *ca = ct_a + (size_t)g.ia * W;
+    const uint32_t *cb = ct_b + (size_t)g.ib * W;
+    for (uint32_t x = threadIdx.x; x < W; x += blockDim.x) {
+        uint32_t v = (uint32_t)g.s1 * ca[x] + (uint32_t)g.s2 * cb[x];
+        if (x == W - 1) v += g.cst - (1u << 30);
+        abar_out[(size_t)blockIdx.x * W + x] = (v + (1u << (sh - 1))) >> sh;
+    }
+}
+
+// ------------------------------------------------------------ key switch
+// One CTA per gate, one thread per output column x in [0, n]: for every party
+// i and coefficient j, round a_{i,j} to ks_bit*t bits, take t base-2^ks_bit
+// digits delta_l and add column x of KS_i[j][l][delta_l - 1] for delta_l != 0.
+__global__ void keyswitch_kernel(LaunchShape S, const uint32_t *__restrict__ ks, const GateDesc *__restrict__ desc,
+                                 const uint32_t *__restrict__ ext, uint32_t *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *ein = reinterpret_cast<uint32_t *>(smem);
+    const uint32_t n = S.n, N = S.N, k = S.k, t = S.t;
+    const uint32_t nb = (1u << S.ks_bit) - 1;
+    const uint32_t E = k * N + 1, W = k * n + 1;
+    const uint32_t round_off = 1u << (32 - S.ks_bit * t - 1);
+    const uint32_t *src = ext + (size_t)blockIdx.x * E;
+    for (uint32_t x = threadIdx.x; x < E; x += blockDim.x) ein[x] = src[x];
+    __syncthreads();
+    const uint32_t orow = desc ? desc[blockIdx.x].out : blockIdx.x;
+    uint32_t *dst = out + (size_t)orow * W;
+    const size_t rowlen = n + 1;
+    const size_t party_stride = (size_t)N * t * nb * rowlen;
+    for (uint32_t x = threadIdx.x; x <= n; x += blockDim.x) {
+        uint32_t bsum = 0;
+        for (uint32_t i = 0; i < k; ++i) {
+            const uint32_t *ksi = ks + i * party_stride + x;
+            uint32_t accv = 0;
+            for (uint32_t j = 0; j < N; ++j) {
+                const uint32_t abar = ein[i * N + j] + round_off;
+                const uint32_t *rowj = ksi + (size_t)j * t * nb * rowlen;
+                for (uint32_t l = 0; l < t; ++l) {
+                    const uint32_t delta = (abar >> (32 - S.ks_bit * (l + 1))) & nb;
+                    if (delta) accv += __ldg(rowj + ((size_t)l * nb + (delta - 1)) * rowlen);
+                }
+            }
+            if (x < n) dst[i * n + x] = accv;
+            else bsum += accv;
+        }
+        if (x == n) dst[k * n] = ein[k * N] + bsum;
+    }
+}
+
+// ------------------------------------------------------------ NOT and descriptors
+__global__ void not_kernel(uint32_t W, const uint32_t *__restrict__ in, uint32_t *__restrict__ out, size_t total) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t v = in[x];
+        out[x] = ((x % W) == W - 1) ? (1u << 30) - v : 0u - v;  // (0, 1/4) - c
+    }
+}
+
+// (cst, s1, s2) of each gate type: AND Eq. 6, OR Eq. 7, NAND Sec. 2.2,
+// NOR Eq. 9 (constant 3/8), XOR Eq. 10, XNOR Eq. 11 (1/2 + 2(c1 - c2)).
+__constant__ uint32_t c_gate_cst[6] = {0xE0000000u, 0x20000000u, 0xA0000000u, 0x60000000u, 0x0u, 0x80000000u};
+__constant__ int32_t c_gate_s1[6] = {1, 1, -1, -1, 2, 2};
+__constant__ int32_t c_gate_s2[6] = {1, 1, -1, -1, -2, -2};
+
+__global__ void desc_types_kernel(const uint8_t *__restrict__ types, GateDesc *__restrict__ desc, uint32_t base,
+                                  uint32_t count) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    uint32_t ty = types[base + g];
+    if (ty > 5) ty = 0;  // validated on the host for mk_gate; defensive here
+    desc[g] = GateDesc{base + g, base + g, c_gate_cst[ty], c_gate_s1[ty], c_gate_s2[ty], base + g};
+}
+
+__global__ void desc_lin_kernel(const mk_lin *__restrict__ lin, GateDesc *__restrict__ desc, uint32_t base,
+                                uint32_t count) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    const mk_lin L = lin[base + g];
+    desc[g] = GateDesc{base + g, base + g, L.cst, L.s1, L.s2, base + g};
+}
+
+__global__ void desc_uniform_kernel(int ty, GateDesc *__restrict__ desc, uint32_t base, uint32_t count) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    desc[g] = GateDesc{base + g, base + g, c_gate_cst[ty], c_gate_s1[ty], c_gate_s2[ty], base + g};
+}
+
+// Independent Goldilocks butterflies in registers: 8 chains per thread so the
+// multiply latency is covered by ILP; the twiddle changes every iteration so
+// nothing is loop-invariant.
+__global__ void butterfly_peak_kernel(uint32_t iters, uint64_t *sink) {
+    constexpr uint64_t P = kGoldilocks, EPS = 0xFFFFFFFFull;
+    uint64_t x[8], y[8];
+    uint64_t w = 0x123456789ull + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        x[c] = (uint64_t)(blockIdx.x * 977 + threadIdx.x * 131 + c) * 0x9E3779B97F4A7C15ull % P;
+        y[c] = x[c] ^ 0x5555;
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint64_t lo = y[c] * w, hi = __umul64hi(y[c], w);
+            const uint64_t hh = hi >> 32, hl = hi & EPS;
+            uint64_t t0 = lo - hh;
+            t0 = (lo < hh) ? t0 - EPS : t0;
+            const uint64_t t1 = hl * EPS;
+            uint64_t V = t0 + t1;
+            V = (V < t1) ? V + EPS : V;
+            V = (V >= P) ? V - P : V;
+            const uint64_t U = x[c];
+            uint64_t s = U + V;
+            s = (s < U) ? s + EPS : s;
+            s = (s >= P) ? s - P : s;
+            uint64_t d = U - V;
+            d = (U < V) ? d - EPS : d;
+            x[c] = s;
+            y[c] = d;
+        }
+        w += 0x10001;
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) r ^= x[c] ^ y[c];
+    if (r == 0x1234567ull) sink[blockIdx.x] = r;  // keeps the loop live; practically never stores
+}
+
+}  // namespace
+
+cudaError_t launch_butterfly_peak(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *sink,
+                                  cudaStream_t st) {
+    butterfly_peak_kernel<<<blocks, threads, 0, st>>>(iters, sink);
+    return cudaGetLastError();
+}
+
+namespace {
+using BootstrapFn = cudaError_t (*)(const LaunchShape &, const DeviceKeys &, const GateDesc *, const uint32_t *,
+                                    const uint32_t *, const uint32_t *, int64_t, uint32_t *, uint32_t *, uint32_t,
+                                    cudaStream_t);
+BootstrapFn pick(const LaunchShape &S) {
+    static const BootstrapFn t8[kNumVariants] = {launch_bootstrap_logn8_v0, launch_bootstrap_logn8_v1,
+                                                 launch_bootstrap_logn8_v2, launch_bootstrap_logn8_v3};
+    static const BootstrapFn t10[kNumVariants] = {launch_bootstrap_logn10_v0, launch_bootstrap_logn10_v1,
+                                                  launch_bootstrap_logn10_v2, launch_bootstrap_logn10_v3};
+    if (S.variant < 0 || S.variant >= kNumVariants) return nullptr;
+    if (S.logN == 8) return t8[S.variant];
+    if (S.logN == 10) return t10[S.variant];
+    return nullptr;
+}
+}  // namespace
+
+cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
+                                 const uint32_t *ct_a, const uint32_t *ct_b, uint32_t *ext, uint32_t count,
+                                 cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    BootstrapFn f = pick(S);
+    if (!f) return cudaErrorInvalidValue;
+    return f(S, K, desc, ct_a, ct_b, nullptr, -1, ext, nullptr, count, st);
+}
+
+cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, const uint32_t *abar,
+                                    uint32_t count, int64_t max_steps, uint32_t *acc, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    BootstrapFn f = pick(S);
+    if (!f) return cudaErrorInvalidValue;
+    return f(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);
+}
+
+cudaError_t launch_modswitch(const LaunchShape &S, const GateDesc *desc, const uint32_t *ct_a,
+                             const uint32_t *ct_b, uint32_t *abar, uint32_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    modswitch_kernel<<<count, 256, 0, st>>>(S, desc, ct_a, ct_b, abar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keyswitch(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
+                             const uint32_t *ext, uint32_t *out, uint32_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const uint32_t threads = ((S.n + 1 + 31) / 32) * 32 > 1024 ? 1024 : ((S.n + 1 + 31) / 32) * 32;
+    const size_t sm = sizeof(uint32_t) * (S.k * S.N + 1);
+    cudaError_t e = cudaFuncSetAttribute(keyswitch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    keyswitch_kernel<<<count, threads, sm, st>>>(S, K.ks, desc, ext, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_not(const LaunchShape &S, const uint32_t *in, uint32_t *out, size_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const uint32_t W = S.k * S.n + 1;
+    const size_t total = count * W;
+    size_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    not_kernel<<<(unsigned)blocks, 256, 0, st>>>(W, in, out, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_desc_from_types(const uint8_t *types, GateDesc *desc, uint32_t base, uint32_t count,
+                                   cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    desc_types_kernel<<<(count + 255) / 256, 256, 0, st>>>(types, desc, base, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_desc_from_lin(const mk_lin *lin, GateDesc *desc, uint32_t base, uint32_t count,
+                                 cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    desc_lin_kernel<<<(count + 255) / 256, 256, 0, st>>>(lin, desc, base, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_desc_uniform(int type, GateDesc *desc, uint32_t base, uint32_t count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    if (type < 0 || type > 5) return cudaErrorInvalidValue;
+    desc_uniform_kernel<<<(count + 255) / 256, 256, 0, st>>>(type, desc, base, count);
+    return cudaGetLastError();
+}
+
+}  // namespace mk
