@@ -132,7 +132,7 @@ def modmuls_per_cmux(P):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mk_bootstrap.cuh", "mk_br_1024.cu"):
+    for f in ("mk_bootstrap.cuh", "mk_br.cu"):
         h.update(open(os.path.join(ROOT, "paper_2205_05825_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
