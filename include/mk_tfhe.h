@@ -203,6 +203,36 @@ int mk_stage_bootstrap(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, co
                        uint32_t *d_ext, size_t count);
 int mk_stage_keyswitch(mk_ctx *ctx, const uint32_t *d_ext, uint32_t *d_out, size_t count);
 
+/* ---------------------------------------------------------------- no allocation */
+/* mk_gates_noalloc: the same gates as mk_gates, for callers that cannot let
+ * the library allocate device memory while they run -- for example a serving
+ * process that reserves all device memory at start-up and forbids later
+ * cudaMalloc, or a latency-critical loop where an allocation could stall or
+ * fail.  The paper has no counterpart; this is an integration aid.
+ *
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine.  Its
+ *    scratch (gate descriptors and the extracted samples between blind
+ *    rotation and key switch) is a fixed device array of
+ *    MK_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
+ *    until the process exits.
+ *  - Capacity: a call takes at most
+ *      floor((MK_NOALLOC_SCRATCH_BYTES - 256) / (4 * (k*N + 1) + 24))
+ *    gates (510 for k = 2, N = 1024; 127 for k = 8).  Larger counts return
+ *    MK_EINVAL before any device work.
+ *  - The context's keys must already be on the device: make one ordinary
+ *    gate call (or mk_autotune) on this context first, otherwise MK_ESTATE.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and it keeps the previous call's
+ *    contents; the kernels write every scratch word before reading it, so
+ *    nothing needs clearing.  Calls whose device work overlaps (different
+ *    streams or contexts on the same GPU) race on the scratch: serialise
+ *    them, e.g. by using one stream. */
+#define MK_NOALLOC_SCRATCH_BYTES (4u << 20)
+int mk_gates_noalloc(mk_ctx *ctx, const uint8_t *d_types, const uint32_t *d_a, const uint32_t *d_b,
+                     uint32_t *d_out, size_t count);
+
 /* ---------------------------------------------------------------- measurement */
 /* Per-kernel timing with CUDA events recorded on the context's stream around
  * every launch of the given kernel class while enabled.  mk_timing_read

@@ -74,6 +74,7 @@ _SIGS = {
     "mk_gates": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_gates_lin": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_not": (ctypes.c_int, [VP, VP, VP, ctypes.c_size_t]),
+    "mk_gates_noalloc": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_stage_modswitch": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_stage_blind_rotate": (ctypes.c_int, [VP, VP, ctypes.c_size_t, ctypes.c_int64, VP]),
     "mk_stage_bootstrap": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
@@ -293,6 +294,12 @@ class Context:
     def gates(self, types, a, b, out):
         self._check(self.L.mk_gates(self.h, _dptr(types), _dptr(a), _dptr(b), _dptr(out), types.numel()),
                     "mk_gates")
+        return out
+
+    def gates_noalloc(self, types, a, b, out):
+        """mk_gates without any device allocation (fixed scratch; see mk_tfhe.h)."""
+        self._check(self.L.mk_gates_noalloc(self.h, _dptr(types), _dptr(a), _dptr(b), _dptr(out), types.numel()),
+                    "mk_gates_noalloc")
         return out
 
     def gates_lin(self, lin, a, b, out):

@@ -993,6 +993,35 @@ int mk_not(mk_ctx *c, const uint32_t *d_a, uint32_t *d_out, size_t count) {
     return MK_OK;
 }
 
+// ------------------------------------------------------------------- no allocation
+int mk_gates_noalloc(mk_ctx *c, const uint8_t *d_types, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+                     size_t count) {
+    if (!c) return MK_EINVAL;
+    if (count == 0) return MK_OK;
+    if (!d_types || !d_a || !d_b || !d_out) return fail(c, MK_EINVAL, "null pointer");
+    if (c->device < 0) return fail(c, MK_EDEVICE, "host-only context (device = -1)");
+    if (c->form != MK_FORM_NTT) return fail(c, MK_EINVAL, "unsupported form");
+    const size_t per_gate = 4 * c->E() + sizeof(GateDesc);
+    const size_t cap = (kNoAllocScratchBytes - 256) / per_gate;
+    if (count > cap)
+        return fail(c, MK_EINVAL, "count " + std::to_string(count) + " exceeds the fixed scratch capacity of " +
+                                      std::to_string(cap) + " gates for these parameters");
+    if (!c->dev_keys_valid)
+        return fail(c, MK_ESTATE, "keys are not on the device yet: make one ordinary gate call on this context first");
+    MK_CUDA(c, cudaSetDevice(c->device));
+    void *base = nullptr;
+    MK_CUDA(c, noalloc_scratch(c->device, &base));
+    GateDesc *desc = reinterpret_cast<GateDesc *>(base);
+    const size_t desc_bytes = ((count * sizeof(GateDesc)) + 255) & ~size_t(255);
+    uint32_t *ext = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(base) + desc_bytes);
+    const uint32_t cnt = (uint32_t)count;
+    cudaError_t e = launch_desc_from_types(d_types, desc, 0, cnt, c->stream);
+    if (e == cudaSuccess) e = launch_bootstrap_ntt(c->shape(), c->dkeys(), desc, d_a, d_b, ext, cnt, c->stream);
+    if (e == cudaSuccess) e = launch_keyswitch(c->shape(), c->dkeys(), desc, ext, d_out, cnt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mk_gates_noalloc");
+    return MK_OK;
+}
+
 // ------------------------------------------------------------------- stages
 int mk_stage_modswitch(mk_ctx *c, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_abar,
                        size_t count) {

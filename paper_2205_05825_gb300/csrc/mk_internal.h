@@ -92,6 +92,11 @@ cudaError_t launch_desc_from_lin(const mk_lin *lin, GateDesc *desc, uint32_t bas
                                  cudaStream_t st);
 cudaError_t launch_desc_uniform(int type, GateDesc *desc, uint32_t base, uint32_t count, cudaStream_t st);
 
+// Fixed device scratch of mk_gates_noalloc (mk_noalloc.cu): its size, and
+// the device address on `device` (current), looked up on first use per device.
+constexpr size_t kNoAllocScratchBytes = MK_NOALLOC_SCRATCH_BYTES;
+cudaError_t noalloc_scratch(int device, void **ptr);
+
 // Register-resident Goldilocks butterfly loop (ALU ceiling measurement).
 // Each thread performs iters * 8 butterflies; sink receives one word per block.
 cudaError_t launch_butterfly_peak(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *sink,
