@@ -1,0 +1,96 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+include/*.h declares; host-only contexts work without a device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mk_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import build
+    build.build()
+    return B.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 30
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2205_05825_gb300 import binding as B
+    assert set(declared_functions()) <= set(B._SIGS)
+
+
+def test_host_only_context_errors_and_presets(lib):
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    assert B.preset("toy", 2) == W.toy_params(2)
+    assert B.preset("full", 2) == W.full_params(2)
+    assert B.preset("full", 4) == W.full_params(4)
+    ctx = B.Context(W.toy_params(2), W.CRS_SEED, device=-1)
+    with pytest.raises(B.MkError, match="MK_ESTATE"):
+        ctx.encrypt(0, np.array([1], np.uint8), 1)
+    with pytest.raises(B.MkError, match="MK_EINVAL"):
+        ctx.keygen(5, 1)
+    ctx.keygen(0, 1)
+    ctx.keygen(1, 2)
+    blob = ctx.save_keys()
+    bad = blob.copy()
+    bad[100] ^= 1
+    ctx2 = B.Context(W.toy_params(2), W.CRS_SEED, device=-1)
+    with pytest.raises(B.MkError, match="MK_EFORMAT"):
+        ctx2.load_keys(bad)
+    with pytest.raises(B.MkError, match="MK_EFORMAT"):
+        ctx2.load_keys(blob[:-9])
+    ctx2.load_keys(blob)
+    assert np.array_equal(ctx2.export_party(1)["bk"], ctx.export_party(1)["bk"])
+    pub = ctx.save_keys(include_secrets=False)
+    ctx3 = B.Context(W.toy_params(2), W.CRS_SEED, device=-1)
+    ctx3.load_keys(pub)
+    with pytest.raises(B.MkError, match="MK_ESTATE"):
+        ctx3.export_party(0, parts=("s",))
+    bad_params = dict(W.toy_params(2), N=512)
+    with pytest.raises(B.MkError, match="MK_EPARAMS"):
+        B.Context(bad_params, 1, device=-1)
+
+
+def test_library_keygen_and_encrypt_byte_equal_to_oracle():
+    """Host key generation and SymEnc of the library equal the oracle's
+    (same seeds, same Philox streams, same Box-Muller samples)."""
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.toy_params(2)
+    keys = o.keygen(P, W.CRS_SEED, W.party_seeds(2))
+    ctx = B.Context(P, W.CRS_SEED, device=-1)
+    for i, s in enumerate(W.party_seeds(2)):
+        ctx.keygen(i, s)
+    assert np.array_equal(ctx.export_crs(), keys.crs)
+    for i in range(2):
+        e = ctx.export_party(i)
+        for nm in ("s", "z", "pk", "bk", "ks"):
+            assert np.array_equal(e[nm], getattr(keys, nm)[i]), nm
+    bits = np.array([0, 1, 1, 0, 1, 0, 0, 1], np.uint8)
+    assert np.array_equal(ctx.encrypt(1, bits, 99), o.encrypt(P, keys, 1, bits, 99))
+    assert np.array_equal(ctx.encrypt_joint(bits, 98), o.encrypt_joint(P, keys, bits, 98))
+    c = o.encrypt(P, keys, 0, bits, 97)
+    assert np.array_equal(ctx.decrypt(c), bits)
+    assert np.array_equal(ctx.phase(c), o.phase(P, keys, c))
