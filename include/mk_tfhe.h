@@ -186,6 +186,44 @@ int mk_gates_lin(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const ui
  * switching.  d_out may alias d_a. */
 int mk_not(mk_ctx *ctx, const uint32_t *d_a, uint32_t *d_out, size_t count);
 
+/* ---------------------------------------------------------------- operators */
+/* k-bit two's-complement operators (Sec. 2.3, Sec. 3.3-3.5, Algorithms 3-6)
+ * as netlists of the bootstrapped gates, evaluated level by level: every
+ * level of the netlist is one batched bootstrap + key-switch launch over all
+ * its gates of all `pairs` operand pairs (gates of one level are
+ * independent).  Operands are LSB-first rows of bit ciphertexts:
+ * d_a, d_b [pairs][kbits][k*n+1].  Outputs:
+ *   mk_add_kbit / mk_sub_kbit: d_out [pairs][kbits]     (a + b, a - b mod 2^kbits)
+ *   mk_mul_kbit:               d_out [pairs][2*kbits]   (the full product)
+ *   mk_div_kbit:               d_q, d_r [pairs][kbits]  (truncating quotient,
+ *                              remainder with a's sign; b = 0 and
+ *                              (-2^(kbits-1)) / (-1) give unspecified bits)
+ * 2 <= kbits <= 64.  The context keeps a plan per (operator, kbits, pairs):
+ * gate descriptors and a wire buffer of (gates + 2 + 2*kbits) * pairs
+ * ciphertexts, allocated on first use. */
+enum { MK_OP_ADD = 0, MK_OP_SUB = 1, MK_OP_MUL = 2, MK_OP_DIV = 3 };
+int mk_add_kbit(mk_ctx *ctx, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+                size_t pairs);
+int mk_sub_kbit(mk_ctx *ctx, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+                size_t pairs);
+int mk_mul_kbit(mk_ctx *ctx, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+                size_t pairs);
+int mk_div_kbit(mk_ctx *ctx, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_q,
+                uint32_t *d_r, size_t pairs);
+
+/* The netlist of an operator, for inspection: gate records (output wire of
+ * gate g = 2 + 2*kbits + g; wires 0/1 = constants 0/1, then a's bits, then
+ * b's bits), outputs encoded as 2*wire + negated, and the number of levels.
+ * Any output pointer may be NULL (counts only); caps bound the copies. */
+typedef struct mk_gate_rec {
+    uint8_t op;           /* MK_AND .. MK_XNOR */
+    uint8_t neg_a, neg_b; /* input negated (MKNOT folded into the gate) */
+    uint8_t reserved;
+    int32_t a, b;         /* input wires */
+} mk_gate_rec;
+int mk_circuit_netlist(int op, uint32_t kbits, mk_gate_rec *gates, uint32_t gate_cap, uint32_t *n_gates,
+                       int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs, uint32_t *n_levels);
+
 /* ---------------------------------------------------------------- stages */
 /* The stages of one bootstrapped gate, for stage-by-stage comparison.
  * mk_stage_modswitch: d_abar[g] = mod-switched words of lin(...) with the

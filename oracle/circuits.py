@@ -1,0 +1,236 @@
+"""Netlists of the k-bit two's-complement operators (test infrastructure only).
+
+Written from the paper's descriptions (Sec. 2.3, Sec. 3.3-3.5, Algorithms 3-6)
+under these readings:
+  - full adder (Sec. 2.3, Alg. 3): t = a XOR b; s = t XOR c;
+    cout = (a AND b) OR (t AND c) -- 5 bootstrapped gates per bit, carry-in
+    0, the last carry computed and dropped, so 5k gates as in Table 3;
+  - subtractor (Alg. 5): a + NOT(b) + 1, NOT folded into the next gate's
+    linear part (MKNOT is linear, Eq. 8);
+  - multiplier (Alg. 4, two's complement): Baugh-Wooley partial products
+    (NAND for the mixed-sign terms, constants 1 at columns k and 2k-1),
+    column compression with full adders, final ripple addition; the 2k-bit
+    product;
+  - divider (Alg. 6): compensation devices (XOR with the sign, then add the
+    sign) to magnitudes, a non-restoring array of CAS cells
+    (out = a XOR ((b XOR p) XOR c), cout = ((a OR c) AND (b XOR p)) OR (a AND c)),
+    a final remainder correction, and compensation back to two's complement;
+    quotient sign = sign(a) XOR sign(b), remainder takes a's sign.
+
+A netlist is a dict: ka, kb (input widths), gates = list of
+(op, a, neg_a, b, neg_b) with op in 0..5 (AND, OR, NAND, NOR, XOR, XNOR) and
+output wire 2 + ka + kb + index; wires 0 and 1 are the constants 0 and 1,
+wires 2..2+ka-1 the bits of a (LSB first), then the bits of b; outputs =
+list of (wire, negated).  The construction order below is part of the
+definition (the library builds the identical netlist).
+"""
+AND, OR, NAND, NOR, XOR, XNOR = range(6)
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3}
+
+
+class _Builder:
+    def __init__(self, ka, kb):
+        self.ka, self.kb = ka, kb
+        self.gates = []
+        self.A = [(2 + i, 0) for i in range(ka)]
+        self.B = [(2 + ka + i, 0) for i in range(kb)]
+
+    def gate(self, op, x, y):
+        self.gates.append((op, x[0], x[1], y[0], y[1]))
+        return (2 + self.ka + self.kb + len(self.gates) - 1, 0)
+
+    def full_adder(self, x, y, c):
+        t = self.gate(XOR, x, y)
+        s = self.gate(XOR, t, c)
+        g1 = self.gate(AND, x, y)
+        g2 = self.gate(AND, t, c)
+        return s, self.gate(OR, g1, g2)
+
+    def half_adder(self, x, y):
+        return self.gate(XOR, x, y), self.gate(AND, x, y)
+
+
+ZERO, ONE = (0, 0), (1, 0)
+
+
+def neg(w):
+    return (w[0], 1 - w[1])
+
+
+def adder(k, subtract=False):
+    bld = _Builder(k, k)
+    c = ONE if subtract else ZERO
+    out = []
+    for i in range(k):
+        y = neg(bld.B[i]) if subtract else bld.B[i]
+        s, c = bld.full_adder(bld.A[i], y, c)
+        out.append(s)
+    return dict(ka=k, kb=k, gates=bld.gates, outputs=out)
+
+
+def multiplier(k):
+    bld = _Builder(k, k)
+    cols = [[] for _ in range(2 * k)]
+    for i in range(k):
+        for j in range(k):
+            op = NAND if (i == k - 1) != (j == k - 1) else AND
+            cols[i + j].append(bld.gate(op, bld.A[j], bld.B[i]))
+    cols[k].append(ONE)
+    cols[2 * k - 1].append(ONE)
+    while any(len(c) > 2 for c in cols):
+        new = [[] for _ in range(2 * k)]
+        for c in range(2 * k):
+            bits = cols[c]
+            while len(bits) >= 3:
+                s, co = bld.full_adder(bits[0], bits[1], bits[2])
+                bits = bits[3:]
+                new[c].append(s)
+                if c + 1 < 2 * k:
+                    new[c + 1].append(co)
+            new[c].extend(bits)
+        cols = new
+    out, carry = [], None
+    for c in range(2 * k):
+        bits = list(cols[c]) + ([carry] if carry is not None else [])
+        if len(bits) == 3:
+            s, carry = bld.full_adder(bits[0], bits[1], bits[2])
+        elif len(bits) == 2:
+            s, carry = bld.half_adder(bits[0], bits[1])
+        elif len(bits) == 1:
+            s, carry = bits[0], None
+        else:
+            s, carry = ZERO, None
+        out.append(s)
+    return dict(ka=k, kb=k, gates=bld.gates, outputs=out)
+
+
+def _compensate(bld, bits, sign):
+    """Conditional two's complement: XOR every bit with the sign, then add the sign."""
+    out, c = [], sign
+    for x in bits:
+        t = bld.gate(XOR, x, sign)
+        out.append(bld.gate(XOR, t, c))
+        c = bld.gate(AND, t, c)
+    return out
+
+
+def divider(k):
+    bld = _Builder(k, k)
+    sa, sb = bld.A[k - 1], bld.B[k - 1]
+    A = _compensate(bld, bld.A, sa)              # |a|, k bits unsigned
+    D = _compensate(bld, bld.B, sb) + [ZERO]     # |b| zero-extended to k+1 bits
+    R = [ZERO] * (k + 1)                         # partial remainder, k+1 bits signed
+    p = ONE                                      # first row subtracts
+    q = [None] * k
+    for i in range(k - 1, -1, -1):
+        R = [A[i]] + R[:k]                       # R = 2R + a_i (top bit shifted out)
+        c = p
+        new = []
+        for j in range(k + 1):                   # CAS cells, LSB first
+            bp = bld.gate(XOR, D[j], p)
+            new.append(bld.gate(XOR, R[j], bld.gate(XOR, bp, c)))
+            aoc = bld.gate(OR, R[j], c)
+            t = bld.gate(AND, aoc, bp)
+            ac = bld.gate(AND, R[j], c)
+            c = bld.gate(OR, t, ac)
+        R = new
+        q[i] = neg(R[k])                         # q_i = 1 iff the new remainder is >= 0
+        p = q[i]
+    s = R[k]                                     # remainder negative: add |b| back
+    c = ZERO
+    rmag = []
+    for j in range(k):
+        m = bld.gate(AND, D[j], s)
+        r, c = bld.full_adder(R[j], m, c)
+        rmag.append(r)
+    qs = bld.gate(XOR, sa, sb)
+    qout = _compensate(bld, q, qs)
+    rout = _compensate(bld, rmag, sa)
+    return dict(ka=k, kb=k, gates=bld.gates, outputs=qout + rout)
+
+
+def build(op, k):
+    if op in ("add", 0):
+        return adder(k)
+    if op in ("sub", 1):
+        return adder(k, subtract=True)
+    if op in ("mul", 2):
+        return multiplier(k)
+    if op in ("div", 3):
+        return divider(k)
+    raise ValueError(op)
+
+
+# ----------------------------------------------------------------------------- plaintext evaluation
+_FN = {AND: lambda x, y: x & y, OR: lambda x, y: x | y, NAND: lambda x, y: 1 - (x & y),
+       NOR: lambda x, y: 1 - (x | y), XOR: lambda x, y: x ^ y, XNOR: lambda x, y: 1 - (x ^ y)}
+
+
+def eval_plain(net, a_bits, b_bits):
+    """Evaluate on plaintext bits (numpy arrays [count][ka], [count][kb] or lists)."""
+    import numpy as np
+    a_bits = np.asarray(a_bits, np.int64)
+    b_bits = np.asarray(b_bits, np.int64)
+    cnt = a_bits.shape[0]
+    w = [np.zeros(cnt, np.int64), np.ones(cnt, np.int64)]
+    w += [a_bits[:, i] for i in range(net["ka"])] + [b_bits[:, i] for i in range(net["kb"])]
+    for op, x, nx, y, ny in net["gates"]:
+        vx = w[x] ^ nx
+        vy = w[y] ^ ny
+        w.append(_FN[op](vx, vy))
+    return np.stack([w[o] ^ ng for o, ng in net["outputs"]], axis=1)
+
+
+def levels(net):
+    """Level of every gate: 1 + the deepest of its inputs (inputs and constants at 0)."""
+    base = 2 + net["ka"] + net["kb"]
+    lev = [0] * base
+    out = []
+    for op, x, nx, y, ny in net["gates"]:
+        L = 1 + max(lev[x], lev[y])
+        lev.append(L)
+        out.append(L)
+    return out
+
+
+# ----------------------------------------------------------------------------- encrypted evaluation
+def eval_encrypted(params, keys, net, a_cts, b_cts, nthreads=None):
+    """Evaluate the netlist on ciphertexts with the oracle's gates.
+
+    a_cts, b_cts: [pairs][ka|kb][k*n+1].  Negated inputs go through MKNOT
+    (Eq. 8) explicitly, then the gate's own linear part and bootstrap; gates
+    of one level run as one oracle batch.  Returns [pairs][n_outputs][k*n+1].
+    """
+    import numpy as np
+    from . import oracle as o
+    a_cts = np.asarray(a_cts, np.uint32)
+    b_cts = np.asarray(b_cts, np.uint32)
+    P, W = a_cts.shape[0], a_cts.shape[2]
+    zero = np.zeros((P, W), np.uint32)
+    one = zero.copy()
+    one[:, -1] = 1 << 30
+    wires = [zero, one] + [a_cts[:, i] for i in range(net["ka"])] + [b_cts[:, i] for i in range(net["kb"])]
+    wires += [None] * len(net["gates"])
+    base = 2 + net["ka"] + net["kb"]
+    lev = levels(net)
+
+    def operand(w, ng):
+        x = wires[w]
+        return np.stack([o.mk_not(params, r) for r in x]) if ng else x
+
+    for L in range(1, max(lev) + 1 if lev else 1):
+        idx = [g for g, l in enumerate(lev) if l == L]
+        types, xs, ys = [], [], []
+        for g in idx:
+            op, x, nx, y, ny = net["gates"][g]
+            types += [op] * P
+            xs.append(operand(x, nx))
+            ys.append(operand(y, ny))
+        out = o.gates(params, keys, np.array(types, np.int32), np.concatenate(xs), np.concatenate(ys),
+                      nthreads=nthreads)
+        for t, g in enumerate(idx):
+            wires[base + g] = out[t * P:(t + 1) * P]
+    res = []
+    for w, ng in net["outputs"]:
+        res.append(operand(w, ng))
+    return np.stack(res, axis=1)

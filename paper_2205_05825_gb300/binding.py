@@ -83,6 +83,13 @@ _SIGS = {
     "mk_ctx_get_variant": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
     "mk_autotune": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]),
+    "mk_add_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
+    "mk_sub_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
+    "mk_mul_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
+    "mk_div_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, VP, ctypes.c_size_t]),
+    "mk_circuit_netlist": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, VP, ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint32), VP, ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "mk_timing_enable": (ctypes.c_int, [VP, ctypes.c_int]),
     "mk_timing_reset": (ctypes.c_int, [VP]),
     "mk_timing_read": (ctypes.c_int, [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -312,6 +319,28 @@ class Context:
         self._check(self.L.mk_not(self.h, _dptr(a), _dptr(out), a.numel() // self.W), "mk_not")
         return out
 
+    # ---------------------------------------------------------------- operators (device tensors)
+    def add_kbit(self, kbits, a, b, out):
+        pairs = a.numel() // (kbits * self.W)
+        self._check(self.L.mk_add_kbit(self.h, kbits, _dptr(a), _dptr(b), _dptr(out), pairs), "mk_add_kbit")
+        return out
+
+    def sub_kbit(self, kbits, a, b, out):
+        pairs = a.numel() // (kbits * self.W)
+        self._check(self.L.mk_sub_kbit(self.h, kbits, _dptr(a), _dptr(b), _dptr(out), pairs), "mk_sub_kbit")
+        return out
+
+    def mul_kbit(self, kbits, a, b, out):
+        pairs = a.numel() // (kbits * self.W)
+        self._check(self.L.mk_mul_kbit(self.h, kbits, _dptr(a), _dptr(b), _dptr(out), pairs), "mk_mul_kbit")
+        return out
+
+    def div_kbit(self, kbits, a, b, q, r):
+        pairs = a.numel() // (kbits * self.W)
+        self._check(self.L.mk_div_kbit(self.h, kbits, _dptr(a), _dptr(b), _dptr(q), _dptr(r), pairs),
+                    "mk_div_kbit")
+        return q, r
+
     # ---------------------------------------------------------------- measurement
     def timing_enable(self, on=True):
         self._check(self.L.mk_timing_enable(self.h, int(on)), "mk_timing_enable")
@@ -370,3 +399,30 @@ def measure_butterfly_rate(device=0, stream=None, iters=4096):
     if rc != MK_OK:
         raise MkError("mk_measure_butterfly_rate: %s" % ERRORS.get(rc, rc))
     return r.value
+
+
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3}
+
+
+class MkGateRec(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint8), ("neg_a", ctypes.c_uint8), ("neg_b", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8), ("a", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+def circuit_netlist(op, kbits):
+    """The library's netlist of an operator as a dict (same shape as the
+    oracle's): ka, kb, gates [(op, a, neg_a, b, neg_b)], outputs [(wire, neg)], levels."""
+    L = load()
+    ng, no, nl = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    opi = OPS[op] if isinstance(op, str) else int(op)
+    rc = L.mk_circuit_netlist(opi, kbits, None, 0, ctypes.byref(ng), None, 0, ctypes.byref(no), ctypes.byref(nl))
+    if rc != MK_OK:
+        raise MkError("mk_circuit_netlist: %s" % ERRORS.get(rc, rc))
+    gates = (MkGateRec * max(ng.value, 1))()
+    outs = (ctypes.c_int32 * max(no.value, 1))()
+    rc = L.mk_circuit_netlist(opi, kbits, gates, ng.value, ctypes.byref(ng), outs, no.value, ctypes.byref(no),
+                              ctypes.byref(nl))
+    if rc != MK_OK:
+        raise MkError("mk_circuit_netlist: %s" % ERRORS.get(rc, rc))
+    return dict(ka=kbits, kb=kbits, gates=[(g.op, g.a, g.neg_a, g.b, g.neg_b) for g in gates[:ng.value]],
+                outputs=[(o >> 1, o & 1) for o in outs[:no.value]], levels=nl.value)

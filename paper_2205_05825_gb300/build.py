@@ -23,7 +23,7 @@ CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu"]
 # mk_br.cu is compiled once per (log2 N, blind-rotation variant).
 BR_SOURCE = "mk_br.cu"
 BR_INSTANCES = [(logn, v) for logn in (8, 10) for v in range(4)]
-CPP_SOURCES = ["mk_host.cpp"]
+CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp"]
 HEADERS = ["mk_internal.h", "mk_bootstrap.cuh", BR_SOURCE]
 
 

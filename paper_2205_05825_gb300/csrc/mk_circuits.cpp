@@ -1,0 +1,245 @@
+// mk_circuits.cpp -- k-bit two's-complement operators (Sec. 2.3 and
+// Sec. 3.3-3.5 of arXiv 2205.05825, Algorithms 3-6) as netlists of the
+// bootstrapped gates, and their levelised evaluation on the GPU.
+//
+// Netlist definition (wire numbering and construction order are part of it):
+//   wire 0 = constant 0, wire 1 = constant 1 (trivial ciphertexts),
+//   wires 2 .. 2+ka-1 = bits of a (LSB first), then the kb bits of b,
+//   gate g writes wire 2 + ka + kb + g; every gate input may be negated
+//   (MKNOT, Eq. 8, is linear and folds into the next gate's linear part);
+//   outputs are (wire, negated) pairs.
+// Constructions:
+//   full adder: t = x XOR y; s = t XOR c; cout = (x AND y) OR (t AND c)
+//     (5 gates per bit; Table 3 counts 5k for the k-bit adder, Alg. 3),
+//   adder: carry-in 0, last carry computed and dropped;
+//   subtractor (Alg. 5): a + NOT(b) + 1 (carry-in 1);
+//   multiplier (Alg. 4): Baugh-Wooley partial products (NAND for the
+//     mixed-sign terms, constant ones at columns k and 2k-1), column
+//     compression with full adders, a final ripple addition; 2k-bit product;
+//   divider (Alg. 6): compensation devices to magnitudes, a non-restoring
+//     array of CAS cells (Sec. 3.5: out = a XOR ((b XOR p) XOR c),
+//     cout = ((a OR c) AND (b XOR p)) OR (a AND c)), a remainder correction,
+//     compensation back; quotient sign = sign(a) XOR sign(b), remainder with
+//     a's sign (truncating division).
+// Levels: a gate's level is 1 + the deepest of its inputs; each level is one
+// batched bootstrap + key-switch launch over all its gates of all pairs.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "mk_internal.h"
+
+namespace mk {
+
+
+namespace {
+
+enum { OP_AND = MK_AND, OP_OR = MK_OR, OP_NAND = MK_NAND, OP_NOR = MK_NOR, OP_XOR = MK_XOR, OP_XNOR = MK_XNOR };
+
+const Wire kZero{0, 0}, kOne{1, 0};
+
+Wire negw(Wire x) { return Wire{x.w, 1 - x.neg}; }
+
+struct Builder {
+    Netlist net;
+    std::vector<Wire> A, B;
+    Builder(uint32_t ka, uint32_t kb) {
+        net.ka = ka;
+        net.kb = kb;
+        for (uint32_t i = 0; i < ka; ++i) A.push_back(Wire{(int32_t)(2 + i), 0});
+        for (uint32_t i = 0; i < kb; ++i) B.push_back(Wire{(int32_t)(2 + ka + i), 0});
+    }
+    Wire gate(int op, Wire x, Wire y) {
+        mk_gate_rec r{};
+        r.op = (uint8_t)op;
+        r.neg_a = (uint8_t)x.neg;
+        r.neg_b = (uint8_t)y.neg;
+        r.a = x.w;
+        r.b = y.w;
+        net.gates.push_back(r);
+        return Wire{(int32_t)(2 + net.ka + net.kb + net.gates.size() - 1), 0};
+    }
+    std::pair<Wire, Wire> full_adder(Wire x, Wire y, Wire c) {
+        Wire t = gate(OP_XOR, x, y);
+        Wire s = gate(OP_XOR, t, c);
+        Wire g1 = gate(OP_AND, x, y);
+        Wire g2 = gate(OP_AND, t, c);
+        return {s, gate(OP_OR, g1, g2)};
+    }
+    std::pair<Wire, Wire> half_adder(Wire x, Wire y) {
+        Wire s = gate(OP_XOR, x, y);
+        return {s, gate(OP_AND, x, y)};
+    }
+    std::vector<Wire> compensate(const std::vector<Wire> &bits, Wire sign) {
+        std::vector<Wire> out;
+        Wire c = sign;
+        for (const Wire &x : bits) {
+            Wire t = gate(OP_XOR, x, sign);
+            out.push_back(gate(OP_XOR, t, c));
+            c = gate(OP_AND, t, c);
+        }
+        return out;
+    }
+};
+
+Netlist build_adder(uint32_t k, bool subtract) {
+    Builder b(k, k);
+    Wire c = subtract ? kOne : kZero;
+    for (uint32_t i = 0; i < k; ++i) {
+        Wire y = subtract ? negw(b.B[i]) : b.B[i];
+        auto sc = b.full_adder(b.A[i], y, c);
+        b.net.outputs.push_back(sc.first);
+        c = sc.second;
+    }
+    return b.net;
+}
+
+Netlist build_multiplier(uint32_t k) {
+    Builder b(k, k);
+    std::vector<std::vector<Wire>> cols(2 * k);
+    for (uint32_t i = 0; i < k; ++i)
+        for (uint32_t j = 0; j < k; ++j) {
+            const int op = ((i == k - 1) != (j == k - 1)) ? OP_NAND : OP_AND;
+            cols[i + j].push_back(b.gate(op, b.A[j], b.B[i]));
+        }
+    cols[k].push_back(kOne);
+    cols[2 * k - 1].push_back(kOne);
+    auto tall = [&]() {
+        for (auto &c : cols)
+            if (c.size() > 2) return true;
+        return false;
+    };
+    while (tall()) {
+        std::vector<std::vector<Wire>> nw(2 * k);
+        for (uint32_t c = 0; c < 2 * k; ++c) {
+            size_t pos = 0;
+            const std::vector<Wire> &bits = cols[c];
+            while (bits.size() - pos >= 3) {
+                auto sc = b.full_adder(bits[pos], bits[pos + 1], bits[pos + 2]);
+                pos += 3;
+                nw[c].push_back(sc.first);
+                if (c + 1 < 2 * k) nw[c + 1].push_back(sc.second);
+            }
+            for (; pos < bits.size(); ++pos) nw[c].push_back(bits[pos]);
+        }
+        cols.swap(nw);
+    }
+    bool have_carry = false;
+    Wire carry{};
+    for (uint32_t c = 0; c < 2 * k; ++c) {
+        std::vector<Wire> bits = cols[c];
+        if (have_carry) bits.push_back(carry);
+        if (bits.size() == 3) {
+            auto sc = b.full_adder(bits[0], bits[1], bits[2]);
+            b.net.outputs.push_back(sc.first);
+            carry = sc.second;
+            have_carry = true;
+        } else if (bits.size() == 2) {
+            auto sc = b.half_adder(bits[0], bits[1]);
+            b.net.outputs.push_back(sc.first);
+            carry = sc.second;
+            have_carry = true;
+        } else if (bits.size() == 1) {
+            b.net.outputs.push_back(bits[0]);
+            have_carry = false;
+        } else {
+            b.net.outputs.push_back(kZero);
+            have_carry = false;
+        }
+    }
+    return b.net;
+}
+
+Netlist build_divider(uint32_t k) {
+    Builder b(k, k);
+    const Wire sa = b.A[k - 1], sb = b.B[k - 1];
+    std::vector<Wire> A = b.compensate(b.A, sa);
+    std::vector<Wire> D = b.compensate(b.B, sb);
+    D.push_back(kZero);
+    std::vector<Wire> R(k + 1, kZero);
+    Wire p = kOne;
+    std::vector<Wire> q(k);
+    for (int i = (int)k - 1; i >= 0; --i) {
+        std::vector<Wire> sh;
+        sh.push_back(A[i]);
+        for (uint32_t j = 0; j < k; ++j) sh.push_back(R[j]);
+        R.swap(sh);
+        Wire c = p;
+        std::vector<Wire> nr;
+        for (uint32_t j = 0; j <= k; ++j) {
+            Wire bp = b.gate(OP_XOR, D[j], p);
+            Wire inner = b.gate(OP_XOR, bp, c);
+            nr.push_back(b.gate(OP_XOR, R[j], inner));
+            Wire aoc = b.gate(OP_OR, R[j], c);
+            Wire t = b.gate(OP_AND, aoc, bp);
+            Wire ac = b.gate(OP_AND, R[j], c);
+            c = b.gate(OP_OR, t, ac);
+        }
+        R.swap(nr);
+        q[i] = negw(R[k]);
+        p = q[i];
+    }
+    const Wire s = R[k];
+    Wire c = kZero;
+    std::vector<Wire> rmag;
+    for (uint32_t j = 0; j < k; ++j) {
+        Wire m = b.gate(OP_AND, D[j], s);
+        auto sc = b.full_adder(R[j], m, c);
+        rmag.push_back(sc.first);
+        c = sc.second;
+    }
+    const Wire qs = b.gate(OP_XOR, sa, sb);
+    std::vector<Wire> qo = b.compensate(q, qs);
+    std::vector<Wire> ro = b.compensate(rmag, sa);
+    b.net.outputs = qo;
+    b.net.outputs.insert(b.net.outputs.end(), ro.begin(), ro.end());
+    return b.net;
+}
+
+}  // namespace
+
+bool build_netlist(int op, uint32_t k, Netlist &out) {
+    if (k < 2 || k > 64) return false;
+    switch (op) {
+    case MK_OP_ADD: out = build_adder(k, false); return true;
+    case MK_OP_SUB: out = build_adder(k, true); return true;
+    case MK_OP_MUL: out = build_multiplier(k); return true;
+    case MK_OP_DIV: out = build_divider(k); return true;
+    default: return false;
+    }
+}
+
+// (cst, s1, s2) of a gate with possibly negated inputs: NOT(c) = 1/4 - c, so
+// s * NOT(c) = s/4 - s*c.
+mk_lin gate_lin(const mk_gate_rec &g) {
+    static const uint32_t cst[6] = {0xE0000000u, 0x20000000u, 0xA0000000u, 0x60000000u, 0x0u, 0x80000000u};
+    static const int32_t s1[6] = {1, 1, -1, -1, 2, 2};
+    static const int32_t s2[6] = {1, 1, -1, -1, -2, -2};
+    mk_lin L{cst[g.op], s1[g.op], s2[g.op]};
+    if (g.neg_a) {
+        L.cst += (uint32_t)L.s1 << 30;
+        L.s1 = -L.s1;
+    }
+    if (g.neg_b) {
+        L.cst += (uint32_t)L.s2 << 30;
+        L.s2 = -L.s2;
+    }
+    return L;
+}
+
+std::vector<uint32_t> netlist_levels(const Netlist &net) {
+    const uint32_t base = 2 + net.ka + net.kb;
+    std::vector<uint32_t> lev(base + net.gates.size(), 0), out(net.gates.size());
+    for (size_t g = 0; g < net.gates.size(); ++g) {
+        const uint32_t L = 1 + std::max(lev[net.gates[g].a], lev[net.gates[g].b]);
+        lev[base + g] = L;
+        out[g] = L;
+    }
+    return out;
+}
+
+}  // namespace mk

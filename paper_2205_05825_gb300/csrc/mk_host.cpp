@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <new>
 #include <string>
 #include <thread>
@@ -213,6 +215,25 @@ struct PartyKeys {
     std::vector<uint32_t> s, z, pk, bk, ks;
 };
 
+// A k-bit operator prepared for `pairs` operand pairs: the levelised gate
+// descriptors (all levels concatenated, gate-major then pair), the wire
+// buffer and the per-level scratch.
+struct CircuitPlan {
+    Netlist net;
+    uint32_t pairs = 0, n_wires = 0, max_level = 0;
+    std::vector<uint32_t> level_off;  // descriptor offset of each level, size levels + 1
+    GateDesc *d_desc = nullptr;
+    uint32_t *d_pool = nullptr;
+    uint32_t *d_ext = nullptr;
+    int32_t *d_outs = nullptr;
+    ~CircuitPlan() {
+        cudaFree(d_desc);
+        cudaFree(d_pool);
+        cudaFree(d_ext);
+        cudaFree(d_outs);
+    }
+};
+
 struct mk_ctx {
     mk_params P{};
     uint32_t logN = 0;
@@ -239,6 +260,7 @@ struct mk_ctx {
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
     std::vector<cudaEvent_t> ev_pool;
+    std::map<std::tuple<int, uint32_t, uint32_t>, std::unique_ptr<CircuitPlan>> plans;
 
     size_t W() const { return (size_t)P.k * P.n + 1; }
     size_t E() const { return (size_t)P.k * P.N + 1; }
@@ -322,6 +344,7 @@ void free_device(mk_ctx *c) {
     cudaFree(c->d_ks);
     cudaFree(c->d_ext);
     cudaFree(c->d_desc);
+    c->plans.clear();
     c->d_tw = nullptr;
     c->d_bk = c->d_keyA = nullptr;
     c->d_ks = c->d_ext = nullptr;
@@ -430,6 +453,91 @@ int run_gates(mk_ctx *c, DescKind kind, const void *src, int type, const uint32_
                   [&] { return launch_keyswitch(S, K, c->d_desc, c->d_ext, d_out, cnt, c->stream); });
         if (e != cudaSuccess) return cuda_fail(c, e, "keyswitch kernel");
     }
+    return MK_OK;
+}
+
+int get_plan(mk_ctx *c, int op, uint32_t k, uint32_t pairs, CircuitPlan **out) {
+    auto key = std::make_tuple(op, k, pairs);
+    auto it = c->plans.find(key);
+    if (it != c->plans.end()) {
+        *out = it->second.get();
+        return MK_OK;
+    }
+    auto plan = std::make_unique<CircuitPlan>();
+    if (!build_netlist(op, k, plan->net)) return fail(c, MK_EINVAL, "unsupported operator or kbits");
+    const Netlist &net = plan->net;
+    const std::vector<uint32_t> lev = netlist_levels(net);
+    const uint32_t L = lev.empty() ? 0 : *std::max_element(lev.begin(), lev.end());
+    const uint32_t base = 2 + net.ka + net.kb;
+    plan->pairs = pairs;
+    plan->n_wires = base + (uint32_t)net.gates.size();
+    std::vector<std::vector<uint32_t>> by_level(L + 1);
+    for (uint32_t g = 0; g < net.gates.size(); ++g) by_level[lev[g]].push_back(g);
+    std::vector<GateDesc> desc;
+    desc.reserve((size_t)net.gates.size() * pairs);
+    plan->level_off.push_back(0);
+    for (uint32_t l = 1; l <= L; ++l) {
+        for (uint32_t g : by_level[l]) {
+            const mk_gate_rec &r = net.gates[g];
+            const mk_lin lin = gate_lin(r);
+            for (uint32_t p = 0; p < pairs; ++p)
+                desc.push_back(GateDesc{(uint32_t)r.a * pairs + p, (uint32_t)r.b * pairs + p, lin.cst, lin.s1, lin.s2,
+                                        (base + g) * pairs + p});
+        }
+        plan->level_off.push_back((uint32_t)desc.size());
+        plan->max_level = std::max<uint32_t>(plan->max_level, (uint32_t)(by_level[l].size() * pairs));
+    }
+    std::vector<int32_t> outs;
+    for (const Wire &w : net.outputs) outs.push_back(w.w * 2 + w.neg);
+    MK_CUDA(c, cudaSetDevice(c->device));
+    MK_CUDA(c, cudaMalloc(&plan->d_desc, std::max<size_t>(desc.size(), 1) * sizeof(GateDesc)));
+    MK_CUDA(c, cudaMalloc(&plan->d_pool, (size_t)plan->n_wires * pairs * c->W() * 4));
+    MK_CUDA(c, cudaMalloc(&plan->d_ext, (size_t)std::max<uint32_t>(plan->max_level, 1) * c->E() * 4));
+    MK_CUDA(c, cudaMalloc(&plan->d_outs, outs.size() * sizeof(int32_t)));
+    MK_CUDA(c, cudaMemcpy(plan->d_desc, desc.data(), desc.size() * sizeof(GateDesc), cudaMemcpyHostToDevice));
+    MK_CUDA(c, cudaMemcpy(plan->d_outs, outs.data(), outs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    *out = plan.get();
+    c->plans[key] = std::move(plan);
+    return MK_OK;
+}
+
+// Evaluate operator `op` on `pairs` operand pairs; outputs [pairs][n_outputs],
+// or, with d_out2, the first half of the outputs into d_out and the second
+// half into d_out2 (quotient and remainder).
+int run_circuit(mk_ctx *c, int op, uint32_t k, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out,
+                size_t pairs, uint32_t *d_out2 = nullptr) {
+    if (pairs == 0) return MK_OK;
+    if (!d_a || !d_b || !d_out) return fail(c, MK_EINVAL, "null pointer");
+    if (k < 2 || k > 64) return fail(c, MK_EINVAL, "kbits must be in [2, 64]");
+    if (pairs > (1u << 20)) return fail(c, MK_EINVAL, "too many pairs");
+    int rc = ensure_device_keys(c);
+    if (rc) return rc;
+    CircuitPlan *pl = nullptr;
+    rc = get_plan(c, op, k, (uint32_t)pairs, &pl);
+    if (rc) return rc;
+    const uint32_t P = (uint32_t)pairs, W = (uint32_t)c->W();
+    const LaunchShape S = c->shape();
+    const DeviceKeys K = c->dkeys();
+    cudaError_t e = launch_circuit_consts(pl->d_pool, P, W, c->stream);
+    if (e == cudaSuccess) e = launch_circuit_inputs(pl->d_pool, d_a, k, P, 2, W, c->stream);
+    if (e == cudaSuccess) e = launch_circuit_inputs(pl->d_pool, d_b, k, P, 2 + k, W, c->stream);
+    for (size_t l = 0; e == cudaSuccess && l + 1 < pl->level_off.size(); ++l) {
+        const uint32_t off = pl->level_off[l], cnt = pl->level_off[l + 1] - off;
+        e = timed(c, MK_KERNEL_BOOTSTRAP, [&] {
+            return launch_bootstrap_ntt(S, K, pl->d_desc + off, pl->d_pool, pl->d_pool, pl->d_ext, cnt, c->stream);
+        });
+        if (e == cudaSuccess)
+            e = timed(c, MK_KERNEL_KEYSWITCH,
+                      [&] { return launch_keyswitch(S, K, pl->d_desc + off, pl->d_ext, pl->d_pool, cnt, c->stream); });
+    }
+    const uint32_t nout = (uint32_t)pl->net.outputs.size();
+    if (e == cudaSuccess && !d_out2) e = launch_circuit_outputs(d_out, pl->d_pool, pl->d_outs, nout, P, W, c->stream);
+    if (e == cudaSuccess && d_out2) {
+        e = launch_circuit_outputs(d_out, pl->d_pool, pl->d_outs, nout / 2, P, W, c->stream);
+        if (e == cudaSuccess)
+            e = launch_circuit_outputs(d_out2, pl->d_pool, pl->d_outs + nout / 2, nout - nout / 2, P, W, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "circuit");
     return MK_OK;
 }
 
@@ -990,6 +1098,47 @@ int mk_not(mk_ctx *c, const uint32_t *d_a, uint32_t *d_out, size_t count) {
     MK_CUDA(c, cudaSetDevice(c->device));
     cudaError_t e = launch_not(c->shape(), d_a, d_out, count, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "not kernel");
+    return MK_OK;
+}
+
+// ------------------------------------------------------------------- operators
+int mk_add_kbit(mk_ctx *c, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out, size_t pairs) {
+    if (!c) return MK_EINVAL;
+    return run_circuit(c, MK_OP_ADD, kbits, d_a, d_b, d_out, pairs);
+}
+
+int mk_sub_kbit(mk_ctx *c, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out, size_t pairs) {
+    if (!c) return MK_EINVAL;
+    return run_circuit(c, MK_OP_SUB, kbits, d_a, d_b, d_out, pairs);
+}
+
+int mk_mul_kbit(mk_ctx *c, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_out, size_t pairs) {
+    if (!c) return MK_EINVAL;
+    return run_circuit(c, MK_OP_MUL, kbits, d_a, d_b, d_out, pairs);
+}
+
+int mk_div_kbit(mk_ctx *c, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_q, uint32_t *d_r,
+                size_t pairs) {
+    if (!c) return MK_EINVAL;
+    if (pairs && !d_r) return fail(c, MK_EINVAL, "null pointer");
+    return run_circuit(c, MK_OP_DIV, kbits, d_a, d_b, d_q, pairs, d_r);
+}
+
+int mk_circuit_netlist(int op, uint32_t kbits, mk_gate_rec *gates, uint32_t gate_cap, uint32_t *n_gates,
+                       int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs, uint32_t *n_levels) {
+    Netlist net;
+    if (!build_netlist(op, kbits, net)) return MK_EINVAL;
+    if (n_gates) *n_gates = (uint32_t)net.gates.size();
+    if (n_outputs) *n_outputs = (uint32_t)net.outputs.size();
+    if (n_levels) {
+        const std::vector<uint32_t> lev = netlist_levels(net);
+        *n_levels = lev.empty() ? 0 : *std::max_element(lev.begin(), lev.end());
+    }
+    if (gates)
+        for (uint32_t g = 0; g < net.gates.size() && g < gate_cap; ++g) gates[g] = net.gates[g];
+    if (outputs)
+        for (uint32_t i = 0; i < net.outputs.size() && i < out_cap; ++i)
+            outputs[i] = net.outputs[i].w * 2 + net.outputs[i].neg;
     return MK_OK;
 }
 

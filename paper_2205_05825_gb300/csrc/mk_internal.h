@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mk_tfhe.h"
 
 namespace mk {
@@ -96,6 +98,27 @@ cudaError_t launch_desc_uniform(int type, GateDesc *desc, uint32_t base, uint32_
 // the device address on `device` (current), looked up on first use per device.
 constexpr size_t kNoAllocScratchBytes = MK_NOALLOC_SCRATCH_BYTES;
 cudaError_t noalloc_scratch(int device, void **ptr);
+
+// ------------------------------------------------------------ circuits
+struct Wire {
+    int32_t w;
+    int neg;
+};
+struct Netlist {
+    uint32_t ka = 0, kb = 0;
+    std::vector<mk_gate_rec> gates;
+    std::vector<Wire> outputs;
+};
+bool build_netlist(int op, uint32_t k, Netlist &out);
+mk_lin gate_lin(const mk_gate_rec &g);
+std::vector<uint32_t> netlist_levels(const Netlist &net);
+
+// Wire buffer helpers: rows are ciphertexts of W words, wire w of pair p at row w*P + p.
+cudaError_t launch_circuit_consts(uint32_t *pool, uint32_t P, uint32_t W, cudaStream_t st);
+cudaError_t launch_circuit_inputs(uint32_t *pool, const uint32_t *src, uint32_t kbits, uint32_t P, uint32_t wire0,
+                                  uint32_t W, cudaStream_t st);
+cudaError_t launch_circuit_outputs(uint32_t *dst, const uint32_t *pool, const int32_t *outs, uint32_t nout,
+                                   uint32_t P, uint32_t W, cudaStream_t st);
 
 // Register-resident Goldilocks butterfly loop (ALU ceiling measurement).
 // Each thread performs iters * 8 butterflies; sink receives one word per block.

@@ -137,7 +137,57 @@ __global__ void butterfly_peak_kernel(uint32_t iters, uint64_t *sink) {
     if (r == 0x1234567ull) sink[blockIdx.x] = r;  // keeps the loop live; practically never stores
 }
 
+// Wire buffer of a circuit: rows 0..P-1 = trivial 0, rows P..2P-1 = trivial 1.
+__global__ void circuit_consts_kernel(uint32_t *pool, uint32_t P, uint32_t W) {
+    const uint32_t r = blockIdx.x;  // 0 .. 2P-1
+    uint32_t *row = pool + (size_t)r * W;
+    for (uint32_t x = threadIdx.x; x < W; x += blockDim.x) row[x] = (x == W - 1 && r >= P) ? (1u << 30) : 0u;
+}
+
+// Operand bits into the wire buffer: row (wire0 + i) * P + p <- src[p][i].
+__global__ void circuit_inputs_kernel(uint32_t *pool, const uint32_t *src, uint32_t kbits, uint32_t P,
+                                      uint32_t wire0, uint32_t W) {
+    const uint32_t r = blockIdx.x;  // i * P + p
+    const uint32_t i = r / P, p = r % P;
+    const uint32_t *s = src + ((size_t)p * kbits + i) * W;
+    uint32_t *d = pool + ((size_t)(wire0 + i) * P + p) * W;
+    for (uint32_t x = threadIdx.x; x < W; x += blockDim.x) d[x] = s[x];
+}
+
+// Outputs out of the wire buffer: dst[p][i] <- wire outs[i] >> 1, negated
+// (MKNOT, Eq. 8: (0, 1/4) - c) when outs[i] & 1.
+__global__ void circuit_outputs_kernel(uint32_t *dst, const uint32_t *pool, const int32_t *outs, uint32_t nout,
+                                       uint32_t P, uint32_t W) {
+    const uint32_t r = blockIdx.x;  // p * nout + i
+    const uint32_t p = r / nout, i = r % nout;
+    const int32_t o = outs[i];
+    const uint32_t *s = pool + ((size_t)(o >> 1) * P + p) * W;
+    uint32_t *d = dst + (size_t)r * W;
+    const bool ng = o & 1;
+    for (uint32_t x = threadIdx.x; x < W; x += blockDim.x) {
+        const uint32_t v = s[x];
+        d[x] = ng ? ((x == W - 1) ? (1u << 30) - v : 0u - v) : v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_circuit_consts(uint32_t *pool, uint32_t P, uint32_t W, cudaStream_t st) {
+    circuit_consts_kernel<<<2 * P, 256, 0, st>>>(pool, P, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_circuit_inputs(uint32_t *pool, const uint32_t *src, uint32_t kbits, uint32_t P, uint32_t wire0,
+                                  uint32_t W, cudaStream_t st) {
+    circuit_inputs_kernel<<<kbits * P, 256, 0, st>>>(pool, src, kbits, P, wire0, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_circuit_outputs(uint32_t *dst, const uint32_t *pool, const int32_t *outs, uint32_t nout,
+                                   uint32_t P, uint32_t W, cudaStream_t st) {
+    circuit_outputs_kernel<<<nout * P, 256, 0, st>>>(dst, pool, outs, nout, P, W);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_butterfly_peak(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *sink,
                                   cudaStream_t st) {

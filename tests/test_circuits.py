@@ -1,0 +1,127 @@
+"""k-bit two's-complement operators (Sec. 2.3, Sec. 3.3-3.5, Alg. 3-6).
+
+Pins: the oracle's netlists against native integer arithmetic (exhaustive
+for 2..5-bit operands, random pairs at 8 and 16 bits); the library's netlists
+are structurally identical to the oracle's; the adder's gate count equals
+Table 3; the oracle's encrypted evaluation decrypts to the native result."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import circuits as C
+from paper_2205_05825_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _wrap(x, bits):
+    x = np.asarray(x, np.int64) % (1 << bits)
+    return np.where(x >= 1 << (bits - 1), x - (1 << bits), x)
+
+
+def expected(op, a, b, k):
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    if op == "add":
+        return _wrap(a + b, k)
+    if op == "sub":
+        return _wrap(a - b, k)
+    if op == "mul":
+        return a * b
+    q = np.trunc(a / np.where(b == 0, 1, b)).astype(np.int64)
+    return q, a - q * b
+
+
+def valid_div(a, b, k):
+    return (np.asarray(b) != 0) & ~((np.asarray(a) == -(1 << (k - 1))) & (np.asarray(b) == -1))
+
+
+def decode(op, out_bits, k):
+    if op == "div":
+        return W.bits_to_int(out_bits[:, :k]), W.bits_to_int(out_bits[:, k:])
+    return W.bits_to_int(out_bits)
+
+
+def operands(k, count=2000):
+    if k <= 5:
+        vals = np.arange(-(1 << (k - 1)), 1 << (k - 1))
+        a, b = np.meshgrid(vals, vals)
+        return a.ravel(), b.ravel()
+    return W.random_operands(k, count)
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 8, 16])
+def test_netlist_plaintext_against_native(op, k):
+    a, b = operands(k)
+    if op == "div":
+        ok = valid_div(a, b, k)
+        a, b = a[ok], b[ok]
+    net = C.build(op, k)
+    got = decode(op, C.eval_plain(net, W.int_to_bits(a, k), W.int_to_bits(b, k)), k)
+    exp = expected(op, a, b, k)
+    if op == "div":
+        assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+    else:
+        assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8, 12, 16])
+def test_library_netlist_equals_oracle_netlist(op, k):
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import build
+    build.build()
+    lib = B.circuit_netlist(op, k)
+    ref = C.build(op, k)
+    assert lib["gates"] == [tuple(g) for g in ref["gates"]]
+    assert lib["outputs"] == [tuple(o) for o in ref["outputs"]]
+    assert lib["levels"] == max(C.levels(ref))
+
+
+def test_gate_counts_against_the_paper():
+    """The adder matches Table 3 (5k).  The subtractor folds NOT into the
+    gates (MKNOT is free, Eq. 8) and so needs 5k, below Table 5's 6k; the
+    multiplier and divider are different netlists of the same operators:
+    their counts are recorded against the paper's, not asserted equal."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table3_table5_gate_counts.txt"))
+            if l.strip() and not l.startswith("#")]
+    for op, k, n in rows:
+        k, n = int(k), int(n)
+        if k < 2:
+            continue
+        ours = len(C.build(op, k)["gates"])
+        if op == "add":
+            assert ours == n
+        elif op == "sub":
+            assert ours == 5 * k and n == 6 * k
+        else:
+            assert ours > 0
+    assert len(C.build("mul", 8)["gates"]) == 325       # paper: 392
+    assert len(C.build("div", 8)["gates"]) == 649       # paper: 7*64 + 17 = 465
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_oracle_encrypted_operators_toy(op):
+    """4-bit operators on ciphertexts (toy set): decrypt to native results."""
+    from oracle import oracle as o
+    from conftest import oracle_keys
+    P = W.toy_params(2)
+    keys = oracle_keys(P)
+    k = 4
+    a = np.array([-8, 7, -3, 5], np.int64)
+    b = np.array([3, -1, -5, 2], np.int64)
+    A = W.int_to_bits(a, k)
+    Bb = W.int_to_bits(b, k)
+    ca = o.encrypt(P, keys, 0, A.ravel(), 501).reshape(len(a), k, -1)
+    cb = o.encrypt(P, keys, 1, Bb.ravel(), 502).reshape(len(a), k, -1)
+    net = C.build(op, k)
+    out = C.eval_encrypted(P, keys, net, ca, cb)
+    bits = o.decrypt(P, keys, out.reshape(-1, out.shape[-1])).reshape(len(a), -1)
+    got = decode(op, bits, k)
+    exp = expected(op, a, b, k)
+    if op == "div":
+        assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+    else:
+        assert np.array_equal(got, exp)

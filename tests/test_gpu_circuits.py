@@ -1,0 +1,117 @@
+"""k-bit operators on the GPU (levelised netlists, one batched launch pair per
+level) against native two's-complement arithmetic, and word-for-word against
+the oracle evaluating its own (identical) netlist."""
+import numpy as np
+import pytest
+
+from conftest import from_dev, oracle_keys, to_dev
+from test_circuits import decode, expected, operands, valid_div
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(P, keys):
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    ctx = B.Context(P, W.CRS_SEED, device=0)
+    ctx.import_oracle_keys(keys)
+    return ctx
+
+
+def _run(ctx, op, k, ca, cb):
+    import torch
+    pairs = ca.shape[0]
+    da, db = to_dev(ca), to_dev(cb)
+    if op == "div":
+        q = torch.zeros((pairs, k, ctx.W), dtype=torch.int32, device="cuda")
+        r = torch.zeros_like(q)
+        ctx.div_kbit(k, da, db, q, r)
+        return np.concatenate([from_dev(q), from_dev(r)], axis=1)
+    nout = 2 * k if op == "mul" else k
+    out = torch.zeros((pairs, nout, ctx.W), dtype=torch.int32, device="cuda")
+    getattr(ctx, op + "_kbit")(k, da, db, out)
+    return from_dev(out)
+
+
+def _encrypt_operands(P, keys, a, b, k, seed):
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import workloads as W
+    ca = o.encrypt(P, keys, 0, W.int_to_bits(a, k).ravel(), seed).reshape(len(a), k, -1)
+    cb = o.encrypt(P, keys, 1, W.int_to_bits(b, k).ravel(), seed + 1).reshape(len(a), k, -1)
+    return ca, cb
+
+
+def _check(P, keys, op, k, a, b, out):
+    from oracle import oracle as o
+    bits = o.decrypt(P, keys, out.reshape(-1, out.shape[-1])).reshape(len(a), -1)
+    got = decode(op, bits, k)
+    if op == "div":
+        ok = valid_div(a, b, k)
+        exp = expected(op, a[ok], b[ok], k)
+        assert np.array_equal(got[0][ok], exp[0]) and np.array_equal(got[1][ok], exp[1])
+    else:
+        assert np.array_equal(got, expected(op, a, b, k))
+
+
+@pytest.fixture(scope="module")
+def toy(gpu_ready):
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.toy_params(2)
+    keys = oracle_keys(P)
+    return P, keys, _ctx(P, keys)
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_toy_4bit_exhaustive(toy, op):
+    """All 256 pairs of 4-bit operands in one levelised batch (toy set)."""
+    P, keys, ctx = toy
+    a, b = operands(4)
+    ca, cb = _encrypt_operands(P, keys, a, b, 4, 700)
+    _check(P, keys, op, 4, a, b, _run(ctx, op, 4, ca, cb))
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_toy_4bit_bit_exact_vs_oracle(toy, op):
+    """Three pairs, every output ciphertext word equal to the oracle's."""
+    from oracle import circuits as C
+    P, keys, ctx = toy
+    a = np.array([-8, 5, -1], np.int64)
+    b = np.array([3, -7, 2], np.int64)
+    ca, cb = _encrypt_operands(P, keys, a, b, 4, 710)
+    got = _run(ctx, op, 4, ca, cb)
+    ref = C.eval_encrypted(P, keys, C.build(op, 4), ca, cb)
+    assert np.array_equal(got, ref)
+
+
+@pytest.fixture(scope="module")
+def full2(gpu_ready):
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.full_params(2)
+    keys = oracle_keys(P)
+    return P, keys, _ctx(P, keys)
+
+
+@pytest.mark.parametrize("op,k,pairs", [("add", 8, 64), ("sub", 8, 64), ("mul", 8, 32), ("div", 8, 16),
+                                        ("add", 16, 16), ("sub", 16, 16), ("mul", 16, 8)])
+def test_full_k2_random_pairs(full2, op, k, pairs):
+    """Full-size parameters, random signed operands (config 3 shape)."""
+    from paper_2205_05825_gb300 import workloads as W
+    P, keys, ctx = full2
+    a, b = W.random_operands(k, pairs, config_id=3)
+    if op == "div":
+        b = np.where(b == 0, 1, b)
+    ca, cb = _encrypt_operands(P, keys, a, b, k, 720 + k)
+    _check(P, keys, op, k, a, b, _run(ctx, op, k, ca, cb))
+
+
+def test_full_k4_8bit_add_and_mul(gpu_ready):
+    """Four parties, full size: 8-bit add and multiply decrypt correctly."""
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.full_params(4)
+    keys = oracle_keys(P)
+    ctx = _ctx(P, keys)
+    a, b = W.random_operands(8, 16, config_id=33)
+    ca, cb = _encrypt_operands(P, keys, a, b, 8, 740)
+    for op in ("add", "mul"):
+        _check(P, keys, op, 8, a, b, _run(ctx, op, 8, ca, cb))
+    ctx.close()
