@@ -121,13 +121,14 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- roofline bookkeeping
-def modmuls_per_cmux(P):
-    """64-bit modular multiplies of one CMux step of the NTT form: (k+2)(d+1)
-    length-N transforms of (N/2) log2 N butterflies, plus (2k+4) d N pointwise
-    products (hybrid product, phase A and B)."""
+def modmuls_per_cmux(P, form="ntt"):
+    """Modular multiplies of one CMux step: (k+2)(d+1) length-N transforms of
+    (N/2) log2 N butterflies, plus (2k+4) d N pointwise products (hybrid
+    product, phase A and B); once per prime (the two-prime form has two)."""
     k, d, N = P["k"], P["d"], P["N"]
     logn = N.bit_length() - 1
-    return (k + 2) * (d + 1) * (N // 2) * logn + (2 * k + 4) * d * N
+    per_prime = (k + 2) * (d + 1) * (N // 2) * logn + (2 * k + 4) * d * N
+    return per_prime * (2 if form == "ntt2" else 1)
 
 
 def kernel_source_hash():
@@ -190,7 +191,8 @@ def run_ours(args):
     d_out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    # autotune the blind-rotation variant on a sample of random ciphertexts
+    # product form, then autotune the blind-rotation variant on a sample of random ciphertexts
+    ctx.set_form(args.form)
     variant, variant_ms = ctx.autotune(min(args.autotune_gates, G))
 
     # warm-up (also uploads the keys)
@@ -269,6 +271,7 @@ def run_ours(args):
     k4 = None
     if args.k4_gates > 0:
         P4, ctx4, t4, a4, b4, tr4 = setup(4, args.k4_gates)
+        ctx4.set_form(args.form)
         ctx4.autotune(min(args.autotune_gates, args.k4_gates))
         dt4, da4, db4 = tdev(t4.astype(np.uint8)), tdev(a4), tdev(b4)
         do4 = torch.zeros((args.k4_gates, ctx4.W), dtype=torch.int32, device="cuda")
@@ -288,15 +291,16 @@ def run_ours(args):
 
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
-    mm_per_gate = modmuls_per_cmux(P) * P["k"] * P["n"]
+    mm_per_gate = modmuls_per_cmux(P, args.form) * P["k"] * P["n"]
     achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / 1e9  # G modmul/s
-    peak = B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048) / 1e9
+    peak = B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / 1e9
     traffic_pg = ncu_traffic_per_gate()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G modmul/s",
                 "frac": achieved / peak, "traffic": (traffic_pg * G if traffic_pg is not None else None),
-                "kernel": "bootstrap_ntt_kernel<10, variant %d>" % variant, "algorithmic_modmuls_per_gate": mm_per_gate,
-                "peak_source": "measured: register-resident Goldilocks butterfly loop on every SM "
-                               "(mk_measure_butterfly_rate), one modmul per butterfly",
+                "kernel": "bootstrap_ntt_kernel<%s, 10, variant %d>" % (args.form, variant), "algorithmic_modmuls_per_gate": mm_per_gate,
+                "peak_source": ("measured: register-resident butterfly loop of the same arithmetic on every SM "
+                                "(mk_measure_butterfly_rate, %s), one modular multiply per butterfly"
+                                % {"ntt": "Goldilocks 64-bit", "ntt2": "Harvey/Shoup mod a 30-bit prime"}[args.form]),
                 "br_share_of_step": br_ms / total_ms if total_ms else None}
 
     ctx.close()
@@ -309,7 +313,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "parties": 2, "gates_per_step": G, "n": P["n"], "N": P["N"],
                    "bg_bit": P["bg_bit"], "d": P["d"], "ks_bit": P["ks_bit"], "t": P["t"],
-                   "sigma_lwe": P["sigma_lwe"], "sigma_rlwe": P["sigma_rlwe"], "form": "ntt64 (exact)",
+                   "sigma_lwe": P["sigma_lwe"], "sigma_rlwe": P["sigma_rlwe"],
+                   "form": {"ntt": "ntt64 (exact, Goldilocks prime)",
+                            "ntt2": "ntt2x30 (exact, two 30-bit primes + CRT)"}[args.form],
                    "variant": variant, "autotune_ms": variant_ms,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "no flush: per-step working set (BK 82 MB NTT domain + KS 110 MB + 37 MB "
@@ -406,6 +412,7 @@ def main():
     ap.add_argument("--k4-gates", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--autotune-gates", type=int, default=2048)
+    ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

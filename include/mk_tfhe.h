@@ -84,11 +84,16 @@ int mk_ctx_destroy(mk_ctx *ctx);
 int mk_ctx_set_stream(mk_ctx *ctx, void *stream);
 int mk_ctx_get_params(const mk_ctx *ctx, mk_params *out);
 
-/* Negacyclic-product form used by the blind rotation. */
+/* Negacyclic-product form used by the blind rotation.  Both are exact (the
+ * product sums are recovered as integers and reduced mod 2^32), so both give
+ * bit-identical ciphertexts.  Changing the form rebuilds the device keys on
+ * the next gate call.  Default: MK_FORM_NTT2. */
 enum {
-    MK_FORM_NTT = 0 /* exact: NTT over the prime 2^64 - 2^32 + 1 (bit-exact) */
+    MK_FORM_NTT = 0, /* NTT over the prime 2^64 - 2^32 + 1 */
+    MK_FORM_NTT2 = 1 /* NTTs over the primes 0x3fff4001 and 0x3ffee001, CRT */
 };
 int mk_ctx_set_form(mk_ctx *ctx, int form);
+int mk_ctx_get_form(const mk_ctx *ctx, int *form);
 
 /* Largest number of gates bootstrapped by one launch (default 4096; the
  * scratch space grows with it).  1 gives the one-gate-per-launch form. */
@@ -281,11 +286,14 @@ int mk_timing_enable(mk_ctx *ctx, int on);
 int mk_timing_reset(mk_ctx *ctx);
 int mk_timing_read(mk_ctx *ctx, int kernel, double *ms_total, uint64_t *launches);
 
-/* ALU ceiling of the NTT form: run a register-resident loop of independent
- * Goldilocks butterflies (one 64-bit modular multiply, add and subtract each)
- * on every SM of `device`; *per_s receives butterflies per second.  No paper
- * counterpart: a measurement aid for the roofline of the blind rotation. */
-int mk_measure_butterfly_rate(int device, void *stream, uint32_t iters, double *per_s);
+/* ALU ceiling of a product form: run a register-resident loop of independent
+ * butterflies on every SM of `device`; *per_s receives butterflies per
+ * second.  form = MK_FORM_NTT: Goldilocks butterflies (one 64-bit modular
+ * multiply, add and subtract); MK_FORM_NTT2: Harvey butterflies modulo a
+ * 30-bit prime (one Shoup multiply, one conditional subtraction, add, sub).
+ * No paper counterpart: a measurement aid for the roofline of the blind
+ * rotation. */
+int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters, double *per_s);
 
 #ifdef __cplusplus
 }

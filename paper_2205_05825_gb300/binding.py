@@ -18,6 +18,7 @@ ERRORS = {-1: "MK_EINVAL", -2: "MK_ENOMEM", -3: "MK_EPARAMS", -4: "MK_ETIMEOUT",
 GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
 PRESETS = {"toy": 0, "full": 1, "paper": 2}
 NUM_VARIANTS = 4
+FORMS = {"ntt": 0, "ntt2": 1}
 
 U32P = ctypes.POINTER(ctypes.c_uint32)
 U8P = ctypes.POINTER(ctypes.c_uint8)
@@ -55,6 +56,7 @@ _SIGS = {
     "mk_ctx_set_stream": (ctypes.c_int, [VP, VP]),
     "mk_ctx_get_params": (ctypes.c_int, [VP, ctypes.POINTER(MkParams)]),
     "mk_ctx_set_form": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_ctx_get_form": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
     "mk_ctx_set_batch": (ctypes.c_int, [VP, ctypes.c_uint32]),
     "mk_last_error": (ctypes.c_char_p, [VP]),
     "mk_sync": (ctypes.c_int, [VP]),
@@ -94,7 +96,7 @@ _SIGS = {
     "mk_timing_reset": (ctypes.c_int, [VP]),
     "mk_timing_read": (ctypes.c_int, [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_uint64)]),
-    "mk_measure_butterfly_rate": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_uint32,
+    "mk_measure_butterfly_rate": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_int, ctypes.c_uint32,
                                                  ctypes.POINTER(ctypes.c_double)]),
 }
 
@@ -196,7 +198,12 @@ class Context:
         self._check(self.L.mk_ctx_set_batch(self.h, n), "mk_ctx_set_batch")
 
     def set_form(self, form):
-        self._check(self.L.mk_ctx_set_form(self.h, form), "mk_ctx_set_form")
+        self._check(self.L.mk_ctx_set_form(self.h, FORMS.get(form, form)), "mk_ctx_set_form")
+
+    def get_form(self):
+        f = ctypes.c_int()
+        self._check(self.L.mk_ctx_get_form(self.h, ctypes.byref(f)), "mk_ctx_get_form")
+        return f.value
 
     def set_variant(self, v):
         self._check(self.L.mk_ctx_set_variant(self.h, v), "mk_ctx_set_variant")
@@ -392,10 +399,12 @@ def lin_records(types):
     return out
 
 
-def measure_butterfly_rate(device=0, stream=None, iters=4096):
-    """Goldilocks butterflies per second on every SM (ALU ceiling of the NTT form)."""
+def measure_butterfly_rate(device=0, stream=None, iters=4096, form="ntt"):
+    """Butterflies per second on every SM: Goldilocks (form "ntt") or Harvey
+    butterflies modulo a 30-bit prime (form "ntt2") -- the ALU ceiling."""
     r = ctypes.c_double()
-    rc = load().mk_measure_butterfly_rate(device, ctypes.c_void_p(stream or 0), iters, ctypes.byref(r))
+    rc = load().mk_measure_butterfly_rate(device, ctypes.c_void_p(stream or 0), FORMS.get(form, form), iters,
+                                          ctypes.byref(r))
     if rc != MK_OK:
         raise MkError("mk_measure_butterfly_rate: %s" % ERRORS.get(rc, rc))
     return r.value

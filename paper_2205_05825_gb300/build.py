@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu"]
 # mk_br.cu is compiled once per (log2 N, blind-rotation variant).
 BR_SOURCE = "mk_br.cu"
-BR_INSTANCES = [(logn, v) for logn in (8, 10) for v in range(4)]
+BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(4)]
 CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp"]
 HEADERS = ["mk_internal.h", "mk_bootstrap.cuh", BR_SOURCE]
 
@@ -46,11 +46,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
                "-I", INCLUDE, *ptxas_v, "-c", os.path.join(CSRC, src), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs.append(obj)
-    for logn, v in BR_INSTANCES:
-        obj = os.path.join(OUT_DIR, "mk_br_%d_v%d.o" % (logn, v))
+    for logn, f, v in BR_INSTANCES:
+        obj = os.path.join(OUT_DIR, "mk_br_%d_f%d_v%d.o" % (logn, f, v))
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-               "-DMK_LOGN=%d" % logn, "-DMK_VARIANT=%d" % v, *ptxas_v, "-c", os.path.join(CSRC, BR_SOURCE),
-               "-o", obj]
+               "-DMK_LOGN=%d" % logn, "-DMK_FIELD=%d" % f, "-DMK_VARIANT=%d" % v, *ptxas_v, "-c",
+               os.path.join(CSRC, BR_SOURCE), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs.append(obj)
     for src in CPP_SOURCES:

@@ -18,6 +18,15 @@
 // CMux loop, and its passes run in a rolled loop (three radix-2 stages per
 // pass in registers, compile-time butterfly patterns D = 4, 2, 1).
 //
+// Two exact fields implement the transform (template parameter F):
+//   FieldGold: the prime p = 2^64 - 2^32 + 1, one 64-bit residue per element;
+//   FieldDual: two 30-bit primes p1, p2 (p1 p2 > 2^59 > 2 |sum|), a pair of
+//     32-bit residues per element, recombined by CRT after the inverse
+//     transform.  Twiddles use Shoup's precomputed quotients and Harvey's lazy
+//     butterflies (values kept in [0, 4p)); keys are stored in Montgomery
+//     form (times 2^32 mod p) so a pointwise product is three multiply-adds.
+// Both give the exact integer product sums, hence identical ciphertexts.
+//
 // Paper steps (arXiv 2205.05825): gate linear part (Sec. 3.1, Eq. 6-11,
 // Algorithms 1-2), gate bootstrapping GB (Sec. 2.2).  The hybrid product
 // follows the MKTFHE construction the paper builds on (named in Sec. 2.2):
@@ -80,24 +89,119 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
     return d;
 }
 
-__device__ __forceinline__ uint64_t digit_to_field(int32_t u) {
-    return u >= 0 ? (uint64_t)u : P - (uint64_t)(-(int64_t)u);
+struct FieldGold {
+    using E = uint64_t;   // element
+    using Tw = uint64_t;  // twiddle
+    static constexpr int kForm = 0;
+    __device__ static __forceinline__ E zero() { return 0; }
+    __device__ static __forceinline__ E from_digit(int32_t u) {
+        return u >= 0 ? (uint64_t)u : P - (uint64_t)(-(int64_t)u);
+    }
+    // Cooley-Tukey: (X, Y) <- (X + S Y, X - S Y)
+    __device__ static __forceinline__ void fwd(E &X, E &Y, const Tw &S) {
+        const uint64_t U = X, V = gmul(Y, S);
+        X = add1(U, V);
+        Y = sub1(U, V);
+    }
+    // Gentleman-Sande: (X, Y) <- (X + Y, S (X - Y))
+    __device__ static __forceinline__ void inv(E &X, E &Y, const Tw &S) {
+        const uint64_t U = X, V = Y;
+        X = add2(U, V);
+        Y = gmul(sub2(U, V), S);
+    }
+    // acc += x * k (k a key word)
+    __device__ static __forceinline__ void mac(E &acc, const E &x, const E &k) { acc = add1(acc, gmul(x, k)); }
+    // Field element of an exact integer in (-p/2, p/2) -> that integer mod 2^32 (p = 1 mod 2^32).
+    __device__ static __forceinline__ uint32_t to_u32(E y) {
+        if (y >= P) y -= P;
+        return (uint32_t)y - (y > HALF_P ? 1u : 0u);
+    }
+};
+
+// ------------------------------------------------------------ two 30-bit primes
+constexpr uint32_t P1 = kP1, P2 = kP2;
+constexpr uint32_t TWO_P1 = 2 * kP1, TWO_P2 = 2 * kP2;
+// -p^-1 mod 2^32 (Montgomery), by Newton iteration at compile time.
+constexpr uint32_t neg_inv32(uint32_t p) {
+    uint32_t x = p;  // p * p = 1 mod 8
+    for (int i = 0; i < 5; ++i) x *= 2u - p * x;
+    return 0u - x;
+}
+constexpr uint32_t PINV1 = neg_inv32(kP1), PINV2 = neg_inv32(kP2);
+constexpr uint64_t P12 = (uint64_t)kP1 * kP2;
+constexpr uint64_t HALF_P12 = P12 >> 1;
+constexpr uint32_t modpow32(uint64_t b, uint64_t e, uint32_t m) {
+    uint64_t r = 1;
+    b %= m;
+    while (e) {
+        if (e & 1) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+constexpr uint32_t CRT_C = modpow32(kP1, kP2 - 2, kP2);                         // p1^-1 mod p2
+constexpr uint32_t CRT_CP = (uint32_t)(((uint64_t)CRT_C << 32) / kP2);           // Shoup companion
+
+// Shoup: x * w mod p in [0, 2p) for any x < 2^32, w < p, wp = floor(w 2^32 / p).
+__device__ __forceinline__ uint32_t shoup(uint32_t x, uint32_t w, uint32_t wp, uint32_t p) {
+    const uint32_t q = __umulhi(x, wp);
+    return x * w - q * p;
 }
 
-// Field element (any representative < 2^64) of an exact integer in
-// (-p/2, p/2) -> that integer mod 2^32 (p = 1 mod 2^32).
-__device__ __forceinline__ uint32_t field_to_u32(uint64_t y) {
-    if (y >= P) y -= P;
-    return (uint32_t)y - (y > HALF_P ? 1u : 0u);
+__device__ __forceinline__ uint32_t red2p(uint32_t x, uint32_t twop) { return min(x, x - twop); }
+
+// Montgomery: x * k * 2^-32 mod p in [0, 2p) for x < 4p, k < p.
+__device__ __forceinline__ uint32_t montmul(uint32_t x, uint32_t k, uint32_t p, uint32_t pinv) {
+    const uint64_t t = (uint64_t)x * k;
+    const uint32_t m = (uint32_t)t * pinv;
+    return (uint32_t)((t + (uint64_t)m * p) >> 32);
 }
 
-__device__ __forceinline__ void load8(const uint64_t *__restrict__ src, uint64_t (&v)[8]) {
-    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
+struct FieldDual {
+    using E = uint2;   // (residue mod p1, residue mod p2)
+    using Tw = uint4;  // (w1, w2, w1', w2')
+    static constexpr int kForm = 1;
+    __device__ static __forceinline__ E zero() { return make_uint2(0, 0); }
+    __device__ static __forceinline__ E from_digit(int32_t u) {
+        return u >= 0 ? make_uint2((uint32_t)u, (uint32_t)u) : make_uint2(P1 + u, P2 + u);
+    }
+    // Harvey: inputs in [0, 4p), outputs in [0, 4p).
+    __device__ static __forceinline__ void fwd(E &X, E &Y, const Tw &S) {
+        const uint32_t x1 = red2p(X.x, TWO_P1), x2 = red2p(X.y, TWO_P2);
+        const uint32_t t1 = shoup(Y.x, S.x, S.z, P1), t2 = shoup(Y.y, S.y, S.w, P2);
+        X = make_uint2(x1 + t1, x2 + t2);
+        Y = make_uint2(x1 - t1 + TWO_P1, x2 - t2 + TWO_P2);
+    }
+    // Inputs and outputs in [0, 2p).
+    __device__ static __forceinline__ void inv(E &X, E &Y, const Tw &S) {
+        const uint32_t u1 = X.x, u2 = X.y, v1 = Y.x, v2 = Y.y;
+        X = make_uint2(red2p(u1 + v1, TWO_P1), red2p(u2 + v2, TWO_P2));
+        Y = make_uint2(shoup(u1 - v1 + TWO_P1, S.x, S.z, P1), shoup(u2 - v2 + TWO_P2, S.y, S.w, P2));
+    }
+    // acc in [0, 2p), x in [0, 4p), k in Montgomery form.
+    __device__ static __forceinline__ void mac(E &acc, const E &x, const E &k) {
+        acc.x = red2p(acc.x + montmul(x.x, k.x, P1, PINV1), TWO_P1);
+        acc.y = red2p(acc.y + montmul(x.y, k.y, P2, PINV2), TWO_P2);
+    }
+    // CRT (Garner) of residues in [0, 2p) to the exact integer in (-p1p2/2, p1p2/2), mod 2^32.
+    __device__ static __forceinline__ uint32_t to_u32(E y) {
+        const uint32_t x1 = min(y.x, y.x - P1), x2 = min(y.y, y.y - P2);
+        uint32_t t = shoup(x2 + TWO_P2 - x1, CRT_C, CRT_CP, P2);
+        t = min(t, t - P2);
+        const uint64_t X = (uint64_t)t * P1 + x1;
+        return (uint32_t)X - (X > HALF_P12 ? (uint32_t)P12 : 0u);
+    }
+};
+
+template <class E>
+__device__ __forceinline__ void load8(const E *__restrict__ src, E (&v)[8]) {
+    static_assert(sizeof(E) == 8, "8-byte elements");
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        ulonglong2 t = __ldg(s2 + q);
-        v[2 * q] = t.x;
-        v[2 * q + 1] = t.y;
+        const uint4 t = __ldg(s4 + q);
+        reinterpret_cast<uint4 *>(v)[q] = t;
     }
 }
 
@@ -118,8 +222,10 @@ __device__ __forceinline__ int jbase(int tid, int LO) {
     return (tid & ((1 << LO) - 1)) | ((tid >> LO) << (LO + 3));
 }
 
-template <int LOGN>
+template <class F, int LOGN>
 struct Ntt {
+    using E = typename F::E;
+    using Tw = typename F::Tw;
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / 8;
     static constexpr int PN = N + N / 16;  // padded polynomial stride in xbuf
@@ -127,43 +233,31 @@ struct Ntt {
     // Forward stage at bit b (distance 2^b) inside a pass with element bits
     // [LO, LO+3): element pairs (c, c + D), D = 2^(b - LO).
     template <int NP, int D>
-    __device__ static __forceinline__ void fwd_stage(uint64_t (&x)[NP][8], int jb, int LO, int b,
-                                                     const uint64_t *tw) {
+    __device__ static __forceinline__ void fwd_stage(E (&x)[NP][8], int jb, int LO, int b, const Tw *tw) {
         const int m = 1 << (LOGN - 1 - b);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (c & D) continue;
-            const uint64_t S = tw[m + ((jb | (c << LO)) >> (b + 1))];
+            const Tw S = tw[m + ((jb | (c << LO)) >> (b + 1))];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const uint64_t U = x[p][c];
-                const uint64_t V = gmul(x[p][c + D], S);
-                x[p][c] = add1(U, V);
-                x[p][c + D] = sub1(U, V);
-            }
+            for (int p = 0; p < NP; ++p) F::fwd(x[p][c], x[p][c + D], S);
         }
     }
 
     template <int NP, int D>
-    __device__ static __forceinline__ void inv_stage(uint64_t (&x)[NP][8], int jb, int LO, int b,
-                                                     const uint64_t *tw) {
+    __device__ static __forceinline__ void inv_stage(E (&x)[NP][8], int jb, int LO, int b, const Tw *tw) {
         const int m = 1 << (LOGN - 1 - b);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (c & D) continue;
-            const uint64_t S = tw[m + ((jb | (c << LO)) >> (b + 1))];
+            const Tw S = tw[m + ((jb | (c << LO)) >> (b + 1))];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const uint64_t U = x[p][c];
-                const uint64_t V = x[p][c + D];
-                x[p][c] = add2(U, V);
-                x[p][c + D] = gmul(sub2(U, V), S);
-            }
+            for (int p = 0; p < NP; ++p) F::inv(x[p][c], x[p][c + D], S);
         }
     }
 
     template <int NP>
-    __device__ static __forceinline__ void exchange(uint64_t (&x)[NP][8], int tid, uint64_t *buf, int LOf, int LOt) {
+    __device__ static __forceinline__ void exchange(E (&x)[NP][8], int tid, E *buf, int LOf, int LOt) {
         const int bf = jbase(tid, LOf);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
@@ -180,7 +274,7 @@ struct Ntt {
 
     // natural (layout logN-3) -> bit-reversed (layout 0)
     template <int NP>
-    __device__ static __forceinline__ void forward(uint64_t (&x)[NP][8], int tid, const uint64_t *tw, uint64_t *buf) {
+    __device__ static __forceinline__ void forward(E (&x)[NP][8], int tid, const Tw *tw, E *buf) {
         int prev = LOGN - 3;
 #pragma unroll 1
         for (int hi = LOGN - 1; hi >= 0; hi -= 3) {
@@ -196,7 +290,7 @@ struct Ntt {
 
     // bit-reversed (layout 0) -> natural (layout logN-3), without 1/N
     template <int NP>
-    __device__ static __forceinline__ void inverse(uint64_t (&x)[NP][8], int tid, const uint64_t *tw, uint64_t *buf) {
+    __device__ static __forceinline__ void inverse(E (&x)[NP][8], int tid, const Tw *tw, E *buf) {
         int prev = 0;
 #pragma unroll 1
         for (int lo = 0; lo < LOGN; lo += 3) {
@@ -218,9 +312,9 @@ struct Gadget {
     uint32_t offset;
     uint32_t bg_bit;
     uint32_t mask, half;
-    __device__ __forceinline__ uint64_t digit(uint32_t x, int l) const {
+    __device__ __forceinline__ int32_t digit(uint32_t x, int l) const {
         const uint32_t xp = x + offset;
-        return digit_to_field((int32_t)((xp >> (32 - bg_bit * (l + 1))) & mask) - (int32_t)half);
+        return (int32_t)((xp >> (32 - bg_bit * (l + 1))) & mask) - (int32_t)half;
     }
 };
 
@@ -241,26 +335,28 @@ struct SmemLayout {
     size_t twf, twi, xbuf, acc, abar, total;
 };
 
-template <int LOGN, int NPF>
+template <class F, int LOGN, int NPF>
 __host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
     constexpr int N = 1 << LOGN;
+    using E = typename F::E;
+    using Tw = typename F::Tw;
     SmemLayout L;
     L.twf = 0;
-    L.twi = L.twf + sizeof(uint64_t) * N;
-    L.xbuf = L.twi + sizeof(uint64_t) * N;
-    L.acc = L.xbuf + sizeof(uint64_t) * NPF * (N + N / 16);
+    L.twi = L.twf + sizeof(Tw) * N;
+    L.xbuf = L.twi + sizeof(Tw) * N;
+    L.acc = L.xbuf + sizeof(E) * NPF * (N + N / 16);
     L.abar = L.acc + sizeof(uint32_t) * (k + 1) * N;
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
     return L;
 }
 
-template <int NP>
-__device__ __forceinline__ void mac8(uint64_t (&A)[8], const uint64_t (&x)[8], const uint64_t *__restrict__ key,
-                                     int tid) {
-    uint64_t kv[8];
+template <class F>
+__device__ __forceinline__ void mac8(typename F::E (&A)[8], const typename F::E (&x)[8],
+                                     const typename F::E *__restrict__ key, int tid) {
+    typename F::E kv[8];
     load8(key + tid * 8, kv);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) A[c] = add1(A[c], gmul(x[c], kv[c]));
+    for (int c = 0; c < 8; ++c) F::mac(A[c], x[c], kv[c]);
 }
 
 // One CMux step for party i (1..k) at rotation e:
@@ -268,27 +364,30 @@ __device__ __forceinline__ void mac8(uint64_t (&A)[8], const uint64_t (&x)[8], c
 // Slots q = 0..k are the accumulator polynomials in the order 0, i, others
 // (phase A); slot k+1 is phase B (w = g^-1(v) against f0, f1).  NPF digit
 // polynomials go through one forward transform together.
-template <int LOGN, int NPF>
+template <class F, int LOGN, int NPF>
 __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys &K, const Gadget &G,
-                                          const uint64_t *bk, int i, uint32_t e, uint32_t *acc, uint64_t *xbuf,
-                                          const uint64_t *twf, const uint64_t *twi, int tid) {
-    using NT = Ntt<LOGN>;
+                                          const typename F::E *bk, int i, uint32_t e, uint32_t *acc,
+                                          typename F::E *xbuf, const typename F::Tw *twf,
+                                          const typename F::Tw *twi, int tid) {
+    using NT = Ntt<F, LOGN>;
+    using E = typename F::E;
     constexpr int N = NT::N, T = NT::T;
     const int k = (int)S.k;
-    uint64_t C0[8], CI[8], CJ[8], V[8];
+    const E *keyA = static_cast<const E *>(K.keyA);
+    E C0[8], CI[8], CJ[8], V[8];
     uint32_t vv[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) C0[c] = CI[c] = CJ[c] = V[c] = 0;
+    for (int c = 0; c < 8; ++c) C0[c] = CI[c] = CJ[c] = V[c] = F::zero();
 #pragma unroll 1
     for (int q = 0; q <= k + 1; ++q) {
         const int jj = (q == 0) ? 0 : (q == 1 ? i : (q - 1 < i ? q - 1 : q));  // q <= k only
         if (q >= 2 && q <= k) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) CJ[c] = 0;
+            for (int c = 0; c < 8; ++c) CJ[c] = F::zero();
         }
 #pragma unroll 1
         for (int l0 = 0; l0 < 3; l0 += NPF) {
-            uint64_t x[NPF][8];
+            E x[NPF][8];
             if (q <= k) {
                 const uint32_t *ap = acc + jj * N;
 #pragma unroll
@@ -300,28 +399,28 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
                     if (r >= N) a = 0u - a;
                     const uint32_t D = a - ap[m];
 #pragma unroll
-                    for (int p = 0; p < NPF; ++p) x[p][c] = G.digit(D, l0 + p);
+                    for (int p = 0; p < NPF; ++p) x[p][c] = F::from_digit(G.digit(D, l0 + p));
                 }
             } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
 #pragma unroll
-                    for (int p = 0; p < NPF; ++p) x[p][c] = G.digit(vv[c], l0 + p);
+                    for (int p = 0; p < NPF; ++p) x[p][c] = F::from_digit(G.digit(vv[c], l0 + p));
             }
             NT::template forward<NPF>(x, tid, twf, xbuf);
 #pragma unroll
             for (int p = 0; p < NPF; ++p) {
                 const int l = l0 + p;
                 if (q <= k) {
-                    const uint64_t *kd = bk + l * N;                              // d_l of BK_{i,j}
-                    const uint64_t *ka = K.keyA + ((size_t)jj * 3 + l) * N;       // -a_l or pk_jj[l]
-                    if (q == 0) mac8<NPF>(C0, x[p], kd, tid);
-                    else if (q == 1) mac8<NPF>(CI, x[p], kd, tid);
-                    else mac8<NPF>(CJ, x[p], kd, tid);
-                    mac8<NPF>(V, x[p], ka, tid);
+                    const E *kd = bk + l * N;                              // d_l of BK_{i,j}
+                    const E *ka = keyA + ((size_t)jj * 3 + l) * N;         // -a_l or pk_jj[l]
+                    if (q == 0) mac8<F>(C0, x[p], kd, tid);
+                    else if (q == 1) mac8<F>(CI, x[p], kd, tid);
+                    else mac8<F>(CJ, x[p], kd, tid);
+                    mac8<F>(V, x[p], ka, tid);
                 } else {
-                    mac8<NPF>(C0, x[p], bk + (3 + l) * N, tid);  // f0_l
-                    mac8<NPF>(CI, x[p], bk + (6 + l) * N, tid);  // f1_l
+                    mac8<F>(C0, x[p], bk + (3 + l) * N, tid);  // f0_l
+                    mac8<F>(CI, x[p], bk + (6 + l) * N, tid);  // f1_l
                 }
             }
         }
@@ -333,31 +432,33 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
         const int last = (q == k) ? 1 : (q == k + 1 ? 3 : (q >= 2 ? 0 : -1));
 #pragma unroll 1
         for (int kind = first; kind <= last; ++kind) {
-            uint64_t y[1][8];
+            E y[1][8];
 #pragma unroll
             for (int c = 0; c < 8; ++c)
                 y[0][c] = kind == 0 ? CJ[c] : (kind == 1 ? V[c] : (kind == 2 ? C0[c] : CI[c]));
             NT::template inverse<1>(y, tid, twi, xbuf);
             if (kind == 1) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) vv[c] = field_to_u32(y[0][c]);
+                for (int c = 0; c < 8; ++c) vv[c] = F::to_u32(y[0][c]);
             } else {
                 uint32_t *dst = acc + (kind == 0 ? jj : (kind == 2 ? 0 : i)) * N;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) dst[tid + T * c] += field_to_u32(y[0][c]);
+                for (int c = 0; c < 8; ++c) dst[tid + T * c] += F::to_u32(y[0][c]);
             }
         }
     }
 }
 
 // k*n CMux steps (i = 1..k, j = 0..n-1 ascending).
-template <int LOGN, int NPF>
+template <class F, int LOGN, int NPF>
 __device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const DeviceKeys &K, const uint16_t *abar,
-                                                  uint32_t *acc, uint64_t *xbuf, const uint64_t *twf,
-                                                  const uint64_t *twi, int64_t max_steps, int tid) {
+                                                  uint32_t *acc, typename F::E *xbuf, const typename F::Tw *twf,
+                                                  const typename F::Tw *twi, int64_t max_steps, int tid) {
     constexpr int N = 1 << LOGN;
+    using E = typename F::E;
     const int n = (int)S.n, k = (int)S.k;
     const Gadget G = make_gadget(S.bg_bit);
+    const E *bk_all = static_cast<const E *>(K.bk);
     int64_t steps = 0;
 #pragma unroll 1
     for (int i = 1; i <= k; ++i) {
@@ -367,23 +468,25 @@ __device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const De
             ++steps;
             const uint32_t e = abar[(i - 1) * n + j];
             if (e == 0) continue;  // X^0 - 1 = 0: every digit is 0, HP adds nothing
-            const uint64_t *bk = K.bk + ((size_t)((i - 1) * n + j) * 9) * N;
-            cmux_step<LOGN, NPF>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
+            const E *bk = bk_all + ((size_t)((i - 1) * n + j) * 9) * N;
+            cmux_step<F, LOGN, NPF>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
             __syncthreads();
         }
     }
 }
 
-template <int LOGN>
-__device__ __forceinline__ void load_twiddles(const DeviceKeys &K, uint64_t *twf, uint64_t *twi, int tid) {
+template <class F, int LOGN>
+__device__ __forceinline__ void load_twiddles(const DeviceKeys &K, typename F::Tw *twf, typename F::Tw *twi,
+                                              int tid) {
     constexpr int N = 1 << LOGN, T = N / 8;
+    const typename F::Tw *gf = static_cast<const typename F::Tw *>(K.tw_fwd);
+    const typename F::Tw *gi = static_cast<const typename F::Tw *>(K.tw_inv);
     for (int x = tid; x < N; x += T) {
-        twf[x] = K.tw_fwd[x];
-        twi[x] = K.tw_inv[x];
+        twf[x] = gf[x];
+        twi[x] = gi[x];
     }
 }
 
-// ACC = (X^{-bbar} * v, 0, ..., 0), v = sum_m (1/8) X^m.
 template <int LOGN>
 __device__ __forceinline__ void init_acc(uint32_t *acc, uint32_t k, uint32_t bbar, int tid) {
     constexpr int N = 1 << LOGN, T = N / 8;
@@ -426,22 +529,24 @@ __device__ __forceinline__ void sample_extract(const LaunchShape &S, const uint3
 //   abar_in == nullptr: linear part + window shift + modulus switch from desc;
 //   otherwise the mod-switched words are read from abar_in.
 //   acc_out == nullptr: SampleExtract + 1/8 into ext; otherwise the raw ACC.
-template <int LOGN, int NPF, int MINB>
+template <class F, int LOGN, int NPF, int MINB>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
                      const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
                      const uint32_t *__restrict__ abar_in, int64_t max_steps,
                      uint32_t *__restrict__ ext, uint32_t *__restrict__ acc_out) {
     constexpr int N = 1 << LOGN, T = N / 8;
+    using E = typename F::E;
+    using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout<LOGN, NPF>(S.k, S.n);
-    uint64_t *twf = reinterpret_cast<uint64_t *>(smem + L.twf);
-    uint64_t *twi = reinterpret_cast<uint64_t *>(smem + L.twi);
-    uint64_t *xbuf = reinterpret_cast<uint64_t *>(smem + L.xbuf);
+    const SmemLayout L = smem_layout<F, LOGN, NPF>(S.k, S.n);
+    Tw *twf = reinterpret_cast<Tw *>(smem + L.twf);
+    Tw *twi = reinterpret_cast<Tw *>(smem + L.twi);
+    E *xbuf = reinterpret_cast<E *>(smem + L.xbuf);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
     uint16_t *abar = reinterpret_cast<uint16_t *>(smem + L.abar);
     const int tid = threadIdx.x;
-    load_twiddles<LOGN>(K, twf, twi, tid);
+    load_twiddles<F, LOGN>(K, twf, twi, tid);
     if (abar_in) {
         const uint32_t W = S.k * S.n + 1;
         for (uint32_t x = tid; x < W; x += T) abar[x] = (uint16_t)abar_in[(size_t)blockIdx.x * W + x];
@@ -451,7 +556,7 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
     __syncthreads();
     init_acc<LOGN>(acc, S.k, abar[S.k * S.n], tid);
     __syncthreads();
-    blind_rotate_core<LOGN, NPF>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
+    blind_rotate_core<F, LOGN, NPF>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
     __syncthreads();
     if (acc_out) {
         uint32_t *dst = acc_out + (size_t)blockIdx.x * (S.k + 1) * N;
@@ -461,13 +566,13 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
     }
 }
 
-template <int LOGN, int NPF, int MINB>
+template <class F, int LOGN, int NPF, int MINB>
 cudaError_t launch_bootstrap(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                              const uint32_t *ct_a, const uint32_t *ct_b, const uint32_t *abar_in,
                              int64_t max_steps, uint32_t *ext, uint32_t *acc_out, uint32_t count,
                              cudaStream_t st) {
-    const SmemLayout L = smem_layout<LOGN, NPF>(S.k, S.n);
-    auto kern = bootstrap_ntt_kernel<LOGN, NPF, MINB>;
+    const SmemLayout L = smem_layout<F, LOGN, NPF>(S.k, S.n);
+    auto kern = bootstrap_ntt_kernel<F, LOGN, NPF, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     kern<<<count, (1 << LOGN) / 8, L.total, st>>>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);

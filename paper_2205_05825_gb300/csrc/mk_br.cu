@@ -1,15 +1,16 @@
-// Blind-rotation instantiation for one (ring dimension, variant) pair, chosen
-// by the build with -DMK_LOGN=<log2 N> -DMK_VARIANT=<v>; the variant table is
-// in mk_internal.h.
+// Blind-rotation instantiation for one (ring dimension, field, variant),
+// chosen by the build with -DMK_LOGN=<log2 N> -DMK_FIELD=<0|1>
+// -DMK_VARIANT=<v>; field 0 = Goldilocks (MK_FORM_NTT), 1 = two 30-bit primes
+// (MK_FORM_NTT2); the variant table is in mk_internal.h.
 #include "mk_bootstrap.cuh"
 
 #ifndef MK_LOGN
 #error "compile with -DMK_LOGN=<log2 N> -DMK_VARIANT=<v>"
 #endif
 
-#define MK_CAT2(a, b, c, d) a##b##c##d
-#define MK_CAT(a, b, c, d) MK_CAT2(a, b, c, d)
-#define MK_FN MK_CAT(launch_bootstrap_logn, MK_LOGN, _v, MK_VARIANT)
+#define MK_CAT2(a, b, c, d, e, f) a##b##c##d##e##f
+#define MK_CAT(a, b, c, d, e, f) MK_CAT2(a, b, c, d, e, f)
+#define MK_FN MK_CAT(launch_bootstrap_logn, MK_LOGN, _f, MK_FIELD, _v, MK_VARIANT)
 
 namespace mk {
 cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc, const uint32_t *ct_a,
@@ -18,7 +19,12 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
     if (count == 0) return cudaSuccess;
     constexpr int NPF = kVariantNpf[MK_VARIANT];
     constexpr int MINB = kVariantMinBlocks[MK_VARIANT];
-    return br::launch_bootstrap<MK_LOGN, NPF, MINB>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
-                                                    st);
+#if MK_FIELD == 0
+    using F = br::FieldGold;
+#else
+    using F = br::FieldDual;
+#endif
+    return br::launch_bootstrap<F, MK_LOGN, NPF, MINB>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out,
+                                                       count, st);
 }
 }  // namespace mk

@@ -179,6 +179,75 @@ struct HostNtt {
     }
 };
 
+// Negacyclic NTT modulo a 30-bit prime (the two primes of MK_FORM_NTT2),
+// same index conventions as HostNtt.
+struct HostNtt32 {
+    uint32_t p = 0, N = 0, logN = 0;
+    std::vector<uint32_t> psi_rev, psi_inv_rev;
+    uint32_t n_inv = 0;
+    static uint32_t mulm(uint32_t a, uint32_t b, uint32_t p) { return (uint32_t)((uint64_t)a * b % p); }
+    static uint32_t powm(uint64_t b, uint64_t e, uint32_t p) {
+        uint64_t r = 1;
+        b %= p;
+        while (e) {
+            if (e & 1) r = r * b % p;
+            b = b * b % p;
+            e >>= 1;
+        }
+        return (uint32_t)r;
+    }
+    bool init(uint32_t prime, uint32_t n_) {
+        p = prime;
+        N = n_;
+        logN = 0;
+        while ((1u << logN) < N) ++logN;
+        if ((p - 1) % (2 * N) != 0) return false;
+        const uint32_t psi = powm(3, (p - 1) / (2 * N), p);  // 3 generates both primes' groups
+        if (powm(psi, N, p) != p - 1) return false;
+        const uint32_t psi_inv = powm(psi, p - 2, p);
+        psi_rev.assign(N, 0);
+        psi_inv_rev.assign(N, 0);
+        for (uint32_t m = 0; m < N; ++m) {
+            uint32_t r = 0;
+            for (uint32_t b = 0; b < logN; ++b)
+                if (m & (1u << b)) r |= 1u << (logN - 1 - b);
+            psi_rev[m] = powm(psi, r, p);
+            psi_inv_rev[m] = powm(psi_inv, r, p);
+        }
+        n_inv = powm(N, p - 2, p);
+        return true;
+    }
+    void forward(uint32_t *a) const {
+        uint32_t t = N;
+        for (uint32_t m = 1; m < N; m <<= 1) {
+            t >>= 1;
+            for (uint32_t i = 0; i < m; ++i) {
+                const uint32_t j1 = 2 * i * t;
+                const uint32_t S = psi_rev[m + i];
+                for (uint32_t j = j1; j < j1 + t; ++j) {
+                    const uint32_t U = a[j], V = mulm(a[j + t], S, p);
+                    a[j] = (U + V) % p;
+                    a[j + t] = (U + p - V) % p;
+                }
+            }
+        }
+    }
+    // Device form of a key polynomial: NTT of (src mod p), times N^-1, in
+    // Montgomery form (times 2^32 mod p).
+    void to_device(const uint32_t *src, uint32_t *dst, bool negate) const {
+        std::vector<uint32_t> a(N);
+        for (uint32_t j = 0; j < N; ++j) {
+            const uint32_t r = src[j] % p;
+            a[j] = negate ? (r == 0 ? 0 : p - r) : r;
+        }
+        forward(a.data());
+        const uint32_t scale = (uint32_t)(((uint64_t)n_inv << 32) % p);
+        for (uint32_t j = 0; j < N; ++j) dst[j] = mulm(a[j], scale, p);
+    }
+    // Twiddle with its Shoup companion floor(w * 2^32 / p).
+    static uint32_t shoup_companion(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+};
+
 template <class F>
 void parallel_for(size_t count, F &&fn) {
     unsigned nt = std::thread::hardware_concurrency();
@@ -240,15 +309,16 @@ struct mk_ctx {
     uint64_t crs_seed = 0;
     int device = -1;
     cudaStream_t stream = nullptr;
-    int form = MK_FORM_NTT;
-    int variant = 1;
+    int form = MK_FORM_NTT2;
+    int variant = 3;
     uint32_t max_batch = 4096;
     std::vector<uint32_t> crs;
     std::vector<PartyKeys> party;
     HostNtt ntt;
+    HostNtt32 ntt_p1, ntt_p2;
     // device state
     bool dev_keys_valid = false;
-    uint64_t *d_tw = nullptr;   // [2][N]
+    void *d_tw = nullptr;       // [2][N] twiddles (8 or 16 bytes each)
     uint64_t *d_bk = nullptr;   // [k][n][3][d][N]
     uint64_t *d_keyA = nullptr; // [(k+1)][d][N]
     uint32_t *d_ks = nullptr;   // [k][N][t][B'-1][n+1]
@@ -267,8 +337,14 @@ struct mk_ctx {
     size_t pk_words() const { return (size_t)P.d * P.N; }
     size_t bk_words() const { return (size_t)P.n * 3 * P.d * P.N; }
     size_t ks_words() const { return (size_t)P.N * P.t * ((1u << P.ks_bit) - 1) * (P.n + 1); }
-    LaunchShape shape() const { return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant}; }
-    DeviceKeys dkeys() const { return DeviceKeys{d_tw, d_tw + P.N, d_bk, d_keyA, d_ks}; }
+    LaunchShape shape() const {
+        return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form};
+    }
+    DeviceKeys dkeys() const {
+        // twiddles: [2][N] of 8-byte (NTT) or 16-byte (NTT2) entries
+        const size_t half = (form == MK_FORM_NTT2 ? 16 : 8) * (size_t)P.N;
+        return DeviceKeys{d_tw, (const unsigned char *)d_tw + half, d_bk, d_keyA, d_ks};
+    }
 };
 
 namespace {
@@ -374,25 +450,58 @@ int ensure_device_keys(mk_ctx *c) {
     MK_CUDA(c, cudaSetDevice(c->device));
     const uint32_t N = c->P.N, n = c->P.n, k = c->P.k, d = c->P.d;
     const size_t bk_entries = (size_t)k * n * 3 * d;  // polynomials
-    std::vector<uint64_t> h_bk(bk_entries * N), h_keyA((size_t)(k + 1) * d * N), h_tw(2 * (size_t)N);
-    for (uint32_t m = 0; m < N; ++m) {
-        h_tw[m] = c->ntt.psi_rev[m];
-        h_tw[N + m] = c->ntt.psi_inv_rev[m];
-    }
-    parallel_for(bk_entries, [&](size_t e) {
+    const size_t keyA_entries = (size_t)(k + 1) * d;
+    // Both forms store 8 bytes per NTT-domain coefficient.
+    std::vector<uint64_t> h_bk(bk_entries * N), h_keyA(keyA_entries * N);
+    std::vector<unsigned char> h_tw(2 * (size_t)N * 16);
+    // src polynomial of BK entry e and of keyA entry r (negated for the CRS)
+    auto bk_src = [&](size_t e) {
         const uint32_t i = (uint32_t)(e / ((size_t)n * 3 * d));
-        const size_t within = e % ((size_t)n * 3 * d);
-        c->ntt.to_ntt(c->party[i].bk.data() + within * N, h_bk.data() + e * N, false, true);
-    });
-    for (uint32_t l = 0; l < d; ++l) c->ntt.to_ntt(c->crs.data() + (size_t)l * N, h_keyA.data() + (size_t)l * N, true, true);
-    for (uint32_t j = 1; j <= k; ++j)
-        for (uint32_t l = 0; l < d; ++l)
-            c->ntt.to_ntt(c->party[j - 1].pk.data() + (size_t)l * N, h_keyA.data() + ((size_t)j * d + l) * N, false, true);
-    if (!c->d_tw) MK_CUDA(c, cudaMalloc(&c->d_tw, h_tw.size() * 8));
+        return c->party[i].bk.data() + (e % ((size_t)n * 3 * d)) * N;
+    };
+    auto keyA_src = [&](size_t r) {
+        const uint32_t jj = (uint32_t)(r / d), l = (uint32_t)(r % d);
+        return jj == 0 ? c->crs.data() + (size_t)l * N : c->party[jj - 1].pk.data() + (size_t)l * N;
+    };
+    if (c->form == MK_FORM_NTT) {
+        uint64_t *tw = reinterpret_cast<uint64_t *>(h_tw.data());
+        for (uint32_t m = 0; m < N; ++m) {
+            tw[m] = c->ntt.psi_rev[m];
+            tw[N + m] = c->ntt.psi_inv_rev[m];
+        }
+        parallel_for(bk_entries, [&](size_t e) { c->ntt.to_ntt(bk_src(e), h_bk.data() + e * N, false, true); });
+        for (size_t r = 0; r < keyA_entries; ++r) c->ntt.to_ntt(keyA_src(r), h_keyA.data() + r * N, r < d, true);
+    } else {
+        if (!c->ntt_p1.N && !(c->ntt_p1.init(kP1, N) && c->ntt_p2.init(kP2, N)))
+            return fail(c, MK_EPARAMS, "ring dimension not supported by the two-prime NTT");
+        uint32_t *tw = reinterpret_cast<uint32_t *>(h_tw.data());  // [2][N][4]
+        for (uint32_t m = 0; m < N; ++m) {
+            const uint32_t f1 = c->ntt_p1.psi_rev[m], f2 = c->ntt_p2.psi_rev[m];
+            const uint32_t i1 = c->ntt_p1.psi_inv_rev[m], i2 = c->ntt_p2.psi_inv_rev[m];
+            uint32_t *ef = tw + 4 * (size_t)m, *ei = tw + 4 * ((size_t)N + m);
+            ef[0] = f1, ef[1] = f2, ef[2] = HostNtt32::shoup_companion(f1, kP1), ef[3] = HostNtt32::shoup_companion(f2, kP2);
+            ei[0] = i1, ei[1] = i2, ei[2] = HostNtt32::shoup_companion(i1, kP1), ei[3] = HostNtt32::shoup_companion(i2, kP2);
+        }
+        auto dual = [&](const uint32_t *src, uint64_t *dst, bool negate) {
+            std::vector<uint32_t> r1(N), r2(N);
+            c->ntt_p1.to_device(src, r1.data(), negate);
+            c->ntt_p2.to_device(src, r2.data(), negate);
+            uint32_t *o = reinterpret_cast<uint32_t *>(dst);  // uint2 {r1, r2} per coefficient
+            for (uint32_t j = 0; j < N; ++j) {
+                o[2 * j] = r1[j];
+                o[2 * j + 1] = r2[j];
+            }
+        };
+        parallel_for(bk_entries, [&](size_t e) { dual(bk_src(e), h_bk.data() + e * N, false); });
+        for (size_t r = 0; r < keyA_entries; ++r) dual(keyA_src(r), h_keyA.data() + r * N, r < d);
+    }
+    if (!c->d_tw) MK_CUDA(c, cudaMalloc(&c->d_tw, h_tw.size()));
     if (!c->d_bk) MK_CUDA(c, cudaMalloc(&c->d_bk, h_bk.size() * 8));
     if (!c->d_keyA) MK_CUDA(c, cudaMalloc(&c->d_keyA, h_keyA.size() * 8));
     if (!c->d_ks) MK_CUDA(c, cudaMalloc(&c->d_ks, (size_t)k * c->ks_words() * 4));
-    MK_CUDA(c, cudaMemcpy(c->d_tw, h_tw.data(), h_tw.size() * 8, cudaMemcpyHostToDevice));
+    // Work already enqueued may still read the previous keys.
+    MK_CUDA(c, cudaStreamSynchronize(c->stream));
+    MK_CUDA(c, cudaMemcpy(c->d_tw, h_tw.data(), h_tw.size(), cudaMemcpyHostToDevice));
     MK_CUDA(c, cudaMemcpy(c->d_bk, h_bk.data(), h_bk.size() * 8, cudaMemcpyHostToDevice));
     MK_CUDA(c, cudaMemcpy(c->d_keyA, h_keyA.data(), h_keyA.size() * 8, cudaMemcpyHostToDevice));
     for (uint32_t i = 0; i < k; ++i)
@@ -640,8 +749,15 @@ int mk_ctx_get_params(const mk_ctx *c, mk_params *out) {
 
 int mk_ctx_set_form(mk_ctx *c, int form) {
     if (!c) return MK_EINVAL;
-    if (form != MK_FORM_NTT) return fail(c, MK_EINVAL, "unknown product form");
+    if (form != MK_FORM_NTT && form != MK_FORM_NTT2) return fail(c, MK_EINVAL, "unknown product form");
+    if (form != c->form) c->dev_keys_valid = false;  // the NTT-domain keys are rebuilt on next use
     c->form = form;
+    return MK_OK;
+}
+
+int mk_ctx_get_form(const mk_ctx *c, int *form) {
+    if (!c || !form) return MK_EINVAL;
+    *form = c->form;
     return MK_OK;
 }
 
@@ -1149,7 +1265,7 @@ int mk_gates_noalloc(mk_ctx *c, const uint8_t *d_types, const uint32_t *d_a, con
     if (count == 0) return MK_OK;
     if (!d_types || !d_a || !d_b || !d_out) return fail(c, MK_EINVAL, "null pointer");
     if (c->device < 0) return fail(c, MK_EDEVICE, "host-only context (device = -1)");
-    if (c->form != MK_FORM_NTT) return fail(c, MK_EINVAL, "unsupported form");
+
     const size_t per_gate = 4 * c->E() + sizeof(GateDesc);
     const size_t cap = (kNoAllocScratchBytes - 256) / per_gate;
     if (count > cap)
@@ -1263,8 +1379,8 @@ int mk_timing_read(mk_ctx *c, int kernel, double *ms_total, uint64_t *launches) 
     return MK_OK;
 }
 
-int mk_measure_butterfly_rate(int device, void *stream, uint32_t iters, double *per_s) {
-    if (!per_s || iters == 0) return MK_EINVAL;
+int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters, double *per_s) {
+    if (!per_s || iters == 0 || (form != MK_FORM_NTT && form != MK_FORM_NTT2)) return MK_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return MK_EDEVICE;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MK_EDEVICE;
@@ -1276,9 +1392,13 @@ int mk_measure_butterfly_rate(int device, void *stream, uint32_t iters, double *
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     int rc = MK_OK;
-    if (launch_butterfly_peak(blocks, threads, iters / 8 + 1, sink, st) != cudaSuccess) rc = MK_EDEVICE;  // warm-up
+    auto launch = [&](uint32_t it) {
+        return form == MK_FORM_NTT ? launch_butterfly_peak(blocks, threads, it, sink, st)
+                                   : launch_butterfly_peak2(blocks, threads, it, reinterpret_cast<uint32_t *>(sink), st);
+    };
+    if (launch(iters / 8 + 1) != cudaSuccess) rc = MK_EDEVICE;  // warm-up
     cudaEventRecord(a, st);
-    if (launch_butterfly_peak(blocks, threads, iters, sink, st) != cudaSuccess) rc = MK_EDEVICE;
+    if (launch(iters) != cudaSuccess) rc = MK_EDEVICE;
     cudaEventRecord(b, st);
     if (cudaEventSynchronize(b) != cudaSuccess) rc = MK_EDEVICE;
     float ms = 0;

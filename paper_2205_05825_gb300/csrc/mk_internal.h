@@ -11,8 +11,13 @@
 
 namespace mk {
 
-// Goldilocks prime 2^64 - 2^32 + 1: the NTT modulus of the exact product form.
+// Goldilocks prime 2^64 - 2^32 + 1: the NTT modulus of the exact product form
+// MK_FORM_NTT.
 constexpr uint64_t kGoldilocks = 0xFFFFFFFF00000001ull;
+// The two 30-bit primes of MK_FORM_NTT2 (both = 1 mod 4096, p1*p2 > 2^59):
+// residues mod p1 and p2, recombined by CRT.
+constexpr uint32_t kP1 = 1073692673u;  // 0x3fff4001
+constexpr uint32_t kP2 = 1073668097u;  // 0x3ffee001
 
 // Per-gate record consumed by the fused linear + blind-rotation kernel.
 struct GateDesc {
@@ -23,17 +28,22 @@ struct GateDesc {
 };
 
 // Device-resident key material of one context, in the layouts the kernels read.
+// Element type of the NTT-domain arrays by form: MK_FORM_NTT uint64 (mod
+// Goldilocks); MK_FORM_NTT2 uint2 (residues mod kP1, kP2, Montgomery form).
+// Twiddle entries: uint64 (NTT) or uint4 {w1, w2, w1', w2'} with Shoup
+// companions w' = floor(w * 2^32 / p) (NTT2).
 struct DeviceKeys {
-    const uint64_t *tw_fwd;  // [N] psi^bitrev(m), Goldilocks
-    const uint64_t *tw_inv;  // [N] psi^-bitrev(m)
-    const uint64_t *bk;      // [k][n][3][d][N] NTT domain, bit-reversed order, times N^-1
-    const uint64_t *keyA;    // [(k+1)][d][N]: [0] = NTT(-a), [j] = NTT(pk_j), times N^-1
-    const uint32_t *ks;      // [k][N][t][B'-1][n+1] torus32
+    const void *tw_fwd;   // [N] psi^bitrev(m)
+    const void *tw_inv;   // [N] psi^-bitrev(m)
+    const void *bk;       // [k][n][3][d][N] NTT domain, bit-reversed order, times N^-1
+    const void *keyA;     // [(k+1)][d][N]: [0] = NTT(-a), [j] = NTT(pk_j), times N^-1
+    const uint32_t *ks;   // [k][N][t][B'-1][n+1] torus32
 };
 
 struct LaunchShape {
     uint32_t n, N, logN, k, d, bg_bit, ks_bit, t;
     int variant;  // blind-rotation variant (see kVariantNpf)
+    int form;     // MK_FORM_NTT or MK_FORM_NTT2
 };
 
 // a1-a8: linear part, window shift, modulus switch, blind rotation (NTT form),
@@ -63,20 +73,18 @@ constexpr int kVariantMinBlocks[kNumVariants] = {1, 2, 3, 4};
 // gate's linear part and modulus switch come from desc/ct_a/ct_b;
 // acc_out == nullptr: the extracted LWE goes to ext, otherwise the raw
 // accumulator to acc_out.
-#define MK_DECLARE_BOOTSTRAP(LOGN, V)                                                                         \
-    cudaError_t launch_bootstrap_logn##LOGN##_v##V(const LaunchShape &S, const DeviceKeys &K,                 \
-                                                   const GateDesc *desc, const uint32_t *ct_a,                \
-                                                   const uint32_t *ct_b, const uint32_t *abar_in,             \
-                                                   int64_t max_steps, uint32_t *ext, uint32_t *acc_out,       \
-                                                   uint32_t count, cudaStream_t st);
-MK_DECLARE_BOOTSTRAP(8, 0)
-MK_DECLARE_BOOTSTRAP(8, 1)
-MK_DECLARE_BOOTSTRAP(8, 2)
-MK_DECLARE_BOOTSTRAP(8, 3)
-MK_DECLARE_BOOTSTRAP(10, 0)
-MK_DECLARE_BOOTSTRAP(10, 1)
-MK_DECLARE_BOOTSTRAP(10, 2)
-MK_DECLARE_BOOTSTRAP(10, 3)
+#define MK_DECLARE_BOOTSTRAP(LOGN, F, V)                                                                      \
+    cudaError_t launch_bootstrap_logn##LOGN##_f##F##_v##V(const LaunchShape &S, const DeviceKeys &K,           \
+                                                          const GateDesc *desc, const uint32_t *ct_a,         \
+                                                          const uint32_t *ct_b, const uint32_t *abar_in,      \
+                                                          int64_t max_steps, uint32_t *ext, uint32_t *acc_out, \
+                                                          uint32_t count, cudaStream_t st);
+#define MK_DECLARE_BOOTSTRAP_F(LOGN, F) \
+    MK_DECLARE_BOOTSTRAP(LOGN, F, 0) MK_DECLARE_BOOTSTRAP(LOGN, F, 1) MK_DECLARE_BOOTSTRAP(LOGN, F, 2) MK_DECLARE_BOOTSTRAP(LOGN, F, 3)
+MK_DECLARE_BOOTSTRAP_F(8, 0)
+MK_DECLARE_BOOTSTRAP_F(8, 1)
+MK_DECLARE_BOOTSTRAP_F(10, 0)
+MK_DECLARE_BOOTSTRAP_F(10, 1)
 
 // a9: per-party key switch of ext [count][k*N+1] into out rows desc[g].out
 // (or row g when desc == nullptr).
@@ -124,5 +132,8 @@ cudaError_t launch_circuit_outputs(uint32_t *dst, const uint32_t *pool, const in
 // Each thread performs iters * 8 butterflies; sink receives one word per block.
 cudaError_t launch_butterfly_peak(uint32_t blocks, uint32_t threads, uint32_t iters, uint64_t *sink,
                                   cudaStream_t st);
+// Same for Harvey/Shoup butterflies modulo a 30-bit prime (MK_FORM_NTT2).
+cudaError_t launch_butterfly_peak2(uint32_t blocks, uint32_t threads, uint32_t iters, uint32_t *sink,
+                                   cudaStream_t st);
 
 }  // namespace mk

@@ -186,12 +186,17 @@ def test_full_k2_sampled_bit_exact_and_all_decrypt(full2):
     assert np.array_equal(got[idx], ref)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-def test_toy_every_variant_bit_exact(toy, variant):
-    """Each blind-rotation kernel variant gives the oracle's ciphertexts."""
+FORM_VARIANTS = [(f, v) for f in ("ntt", "ntt2") for v in range(4)]
+
+
+@pytest.mark.parametrize("form,variant", FORM_VARIANTS)
+def test_toy_every_variant_bit_exact(toy, form, variant):
+    """Each product form (Goldilocks NTT, two-prime NTT) and each kernel
+    variant gives the oracle's ciphertexts."""
     import torch
     from oracle import oracle as o
     P, keys, ctx, g, b1, b2, c1, c2 = toy
+    ctx.set_form(form)
     ctx.set_variant(variant)
     try:
         out = torch.zeros((len(g), ctx.W), dtype=torch.int32, device="cuda")
@@ -204,11 +209,12 @@ def test_toy_every_variant_bit_exact(toy, variant):
         ref = o.blind_rotate(P, keys, from_dev(abar), max_steps=3)
         assert np.array_equal(from_dev(acc), ref)
     finally:
-        ctx.set_variant(1)
+        ctx.set_form("ntt2")
+        ctx.set_variant(3)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-def test_full_k2_every_variant_sampled(full2, variant):
+@pytest.mark.parametrize("form,variant", FORM_VARIANTS)
+def test_full_k2_every_variant_sampled(full2, form, variant):
     """Full size (n=560, N=1024, k=2): each variant, 96 gates (a ragged last
     wave), 3 sampled gates byte-equal to the oracle, all 96 decrypt."""
     import torch
@@ -219,13 +225,15 @@ def test_full_k2_every_variant_sampled(full2, variant):
     types, b1, b2 = W.random_gates(G, config_id=7)
     c1 = o.encrypt(P, keys, 0, b1, W.encryption_seed(7, 0))
     c2 = o.encrypt(P, keys, 1, b2, W.encryption_seed(7, 1))
+    ctx.set_form(form)
     ctx.set_variant(variant)
     try:
         out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
         ctx.gates(to_dev(types.astype(np.uint8)), to_dev(c1), to_dev(c2), out)
         got = from_dev(out)
     finally:
-        ctx.set_variant(1)
+        ctx.set_form("ntt2")
+        ctx.set_variant(3)
     exp = np.array([TRUTH[int(t)](int(x), int(y)) for t, x, y in zip(types, b1, b2)], np.uint8)
     assert np.array_equal(o.decrypt(P, keys, got), exp)
     idx = np.array([0, 50, 95])
