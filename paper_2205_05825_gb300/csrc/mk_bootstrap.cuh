@@ -22,9 +22,10 @@
 //   FieldGold: the prime p = 2^64 - 2^32 + 1, one 64-bit residue per element;
 //   FieldDual: two 30-bit primes p1, p2 (p1 p2 > 2^59 > 2 |sum|), a pair of
 //     32-bit residues per element, recombined by CRT after the inverse
-//     transform.  Twiddles use Shoup's precomputed quotients and Harvey's lazy
-//     butterflies (values kept in [0, 4p)); keys are stored in Montgomery
-//     form (times 2^32 mod p) so a pointwise product is three multiply-adds.
+//     transform.  Harvey's lazy butterflies (values kept in [0, 4p)) with
+//     Shoup's precomputed quotients for the twiddles (two dependent
+//     multiplies); keys in Montgomery form (times 2^32 mod p), so a pointwise
+//     product is three multiply-adds without a second table.
 // Both give the exact integer product sums, hence identical ciphertexts.
 //
 // Paper steps (arXiv 2205.05825): gate linear part (Sec. 3.1, Eq. 6-11,
@@ -160,7 +161,7 @@ __device__ __forceinline__ uint32_t montmul(uint32_t x, uint32_t k, uint32_t p, 
 
 struct FieldDual {
     using E = uint2;   // (residue mod p1, residue mod p2)
-    using Tw = uint4;  // (w1, w2, w1', w2')
+    using Tw = uint4;  // (w1, w2, w1', w2'): twiddles with Shoup companions
     static constexpr int kForm = 1;
     __device__ static __forceinline__ E zero() { return make_uint2(0, 0); }
     __device__ static __forceinline__ E from_digit(int32_t u) {
@@ -218,14 +219,24 @@ __device__ __forceinline__ void load8(const E *__restrict__ src, E (&v)[8]) {
 // access at the 2-wavefront minimum).
 __device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }
 
+// Twiddle tables are stored with one pad entry every 4, so the stride-2 and
+// stride-4 twiddle reads of the late stages hit distinct banks.
+__device__ __forceinline__ int twp(int t) { return t + (t >> 2); }
+
 __device__ __forceinline__ int jbase(int tid, int LO) {
     return (tid & ((1 << LO) - 1)) | ((tid >> LO) << (LO + 3));
 }
 
-template <class F, int LOGN>
+// TWG: twiddles read from global memory through the read-only cache
+// (unpadded table) instead of a per-CTA shared-memory copy.
+template <class F, int LOGN, bool TWG>
 struct Ntt {
     using E = typename F::E;
     using Tw = typename F::Tw;
+    __device__ static __forceinline__ Tw twiddle(const Tw *tw, int t) {
+        if constexpr (TWG) return __ldg(tw + t);
+        else return tw[twp(t)];
+    }
     static constexpr int N = 1 << LOGN;
     static constexpr int T = N / 8;
     static constexpr int PN = N + N / 16;  // padded polynomial stride in xbuf
@@ -238,7 +249,7 @@ struct Ntt {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (c & D) continue;
-            const Tw S = tw[m + ((jb | (c << LO)) >> (b + 1))];
+            const Tw S = twiddle(tw, m + ((jb | (c << LO)) >> (b + 1)));
 #pragma unroll
             for (int p = 0; p < NP; ++p) F::fwd(x[p][c], x[p][c + D], S);
         }
@@ -250,7 +261,7 @@ struct Ntt {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (c & D) continue;
-            const Tw S = tw[m + ((jb | (c << LO)) >> (b + 1))];
+            const Tw S = twiddle(tw, m + ((jb | (c << LO)) >> (b + 1)));
 #pragma unroll
             for (int p = 0; p < NP; ++p) F::inv(x[p][c], x[p][c + D], S);
         }
@@ -335,15 +346,16 @@ struct SmemLayout {
     size_t twf, twi, xbuf, acc, abar, total;
 };
 
-template <class F, int LOGN, int NPF>
+template <class F, int LOGN, int NPF, bool TWG>
 __host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
     constexpr int N = 1 << LOGN;
     using E = typename F::E;
     using Tw = typename F::Tw;
+    constexpr size_t tw_bytes = TWG ? 0 : sizeof(Tw) * (N + N / 4);
     SmemLayout L;
     L.twf = 0;
-    L.twi = L.twf + sizeof(Tw) * N;
-    L.xbuf = L.twi + sizeof(Tw) * N;
+    L.twi = L.twf + tw_bytes;
+    L.xbuf = L.twi + tw_bytes;
     L.acc = L.xbuf + sizeof(E) * NPF * (N + N / 16);
     L.abar = L.acc + sizeof(uint32_t) * (k + 1) * N;
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
@@ -364,12 +376,12 @@ __device__ __forceinline__ void mac8(typename F::E (&A)[8], const typename F::E 
 // Slots q = 0..k are the accumulator polynomials in the order 0, i, others
 // (phase A); slot k+1 is phase B (w = g^-1(v) against f0, f1).  NPF digit
 // polynomials go through one forward transform together.
-template <class F, int LOGN, int NPF>
+template <class F, int LOGN, int NPF, bool TWG>
 __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys &K, const Gadget &G,
                                           const typename F::E *bk, int i, uint32_t e, uint32_t *acc,
                                           typename F::E *xbuf, const typename F::Tw *twf,
                                           const typename F::Tw *twi, int tid) {
-    using NT = Ntt<F, LOGN>;
+    using NT = Ntt<F, LOGN, TWG>;
     using E = typename F::E;
     constexpr int N = NT::N, T = NT::T;
     const int k = (int)S.k;
@@ -450,7 +462,7 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
 }
 
 // k*n CMux steps (i = 1..k, j = 0..n-1 ascending).
-template <class F, int LOGN, int NPF>
+template <class F, int LOGN, int NPF, bool TWG>
 __device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const DeviceKeys &K, const uint16_t *abar,
                                                   uint32_t *acc, typename F::E *xbuf, const typename F::Tw *twf,
                                                   const typename F::Tw *twi, int64_t max_steps, int tid) {
@@ -469,7 +481,7 @@ __device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const De
             const uint32_t e = abar[(i - 1) * n + j];
             if (e == 0) continue;  // X^0 - 1 = 0: every digit is 0, HP adds nothing
             const E *bk = bk_all + ((size_t)((i - 1) * n + j) * 9) * N;
-            cmux_step<F, LOGN, NPF>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
+            cmux_step<F, LOGN, NPF, TWG>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
             __syncthreads();
         }
     }
@@ -482,8 +494,8 @@ __device__ __forceinline__ void load_twiddles(const DeviceKeys &K, typename F::T
     const typename F::Tw *gf = static_cast<const typename F::Tw *>(K.tw_fwd);
     const typename F::Tw *gi = static_cast<const typename F::Tw *>(K.tw_inv);
     for (int x = tid; x < N; x += T) {
-        twf[x] = gf[x];
-        twi[x] = gi[x];
+        twf[twp(x)] = gf[x];
+        twi[twp(x)] = gi[x];
     }
 }
 
@@ -529,7 +541,7 @@ __device__ __forceinline__ void sample_extract(const LaunchShape &S, const uint3
 //   abar_in == nullptr: linear part + window shift + modulus switch from desc;
 //   otherwise the mod-switched words are read from abar_in.
 //   acc_out == nullptr: SampleExtract + 1/8 into ext; otherwise the raw ACC.
-template <class F, int LOGN, int NPF, int MINB>
+template <class F, int LOGN, int NPF, int MINB, bool TWG>
 __global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
 bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
                      const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
@@ -539,14 +551,20 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
     using E = typename F::E;
     using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout<F, LOGN, NPF>(S.k, S.n);
-    Tw *twf = reinterpret_cast<Tw *>(smem + L.twf);
-    Tw *twi = reinterpret_cast<Tw *>(smem + L.twi);
+    const int tid = threadIdx.x;
+    const SmemLayout L = smem_layout<F, LOGN, NPF, TWG>(S.k, S.n);
+    const Tw *twf, *twi;
+    if constexpr (TWG) {
+        twf = static_cast<const Tw *>(K.tw_fwd);
+        twi = static_cast<const Tw *>(K.tw_inv);
+    } else {
+        twf = reinterpret_cast<Tw *>(smem + L.twf);
+        twi = reinterpret_cast<Tw *>(smem + L.twi);
+        load_twiddles<F, LOGN>(K, reinterpret_cast<Tw *>(smem + L.twf), reinterpret_cast<Tw *>(smem + L.twi), tid);
+    }
     E *xbuf = reinterpret_cast<E *>(smem + L.xbuf);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
     uint16_t *abar = reinterpret_cast<uint16_t *>(smem + L.abar);
-    const int tid = threadIdx.x;
-    load_twiddles<F, LOGN>(K, twf, twi, tid);
     if (abar_in) {
         const uint32_t W = S.k * S.n + 1;
         for (uint32_t x = tid; x < W; x += T) abar[x] = (uint16_t)abar_in[(size_t)blockIdx.x * W + x];
@@ -556,7 +574,7 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
     __syncthreads();
     init_acc<LOGN>(acc, S.k, abar[S.k * S.n], tid);
     __syncthreads();
-    blind_rotate_core<F, LOGN, NPF>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
+    blind_rotate_core<F, LOGN, NPF, TWG>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
     __syncthreads();
     if (acc_out) {
         uint32_t *dst = acc_out + (size_t)blockIdx.x * (S.k + 1) * N;
@@ -566,13 +584,13 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
     }
 }
 
-template <class F, int LOGN, int NPF, int MINB>
+template <class F, int LOGN, int NPF, int MINB, bool TWG>
 cudaError_t launch_bootstrap(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                              const uint32_t *ct_a, const uint32_t *ct_b, const uint32_t *abar_in,
                              int64_t max_steps, uint32_t *ext, uint32_t *acc_out, uint32_t count,
                              cudaStream_t st) {
-    const SmemLayout L = smem_layout<F, LOGN, NPF>(S.k, S.n);
-    auto kern = bootstrap_ntt_kernel<F, LOGN, NPF, MINB>;
+    const SmemLayout L = smem_layout<F, LOGN, NPF, TWG>(S.k, S.n);
+    auto kern = bootstrap_ntt_kernel<F, LOGN, NPF, MINB, TWG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     kern<<<count, (1 << LOGN) / 8, L.total, st>>>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);

@@ -19,12 +19,13 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
     if (count == 0) return cudaSuccess;
     constexpr int NPF = kVariantNpf[MK_VARIANT];
     constexpr int MINB = kVariantMinBlocks[MK_VARIANT];
+    constexpr bool TWG = kVariantTwg[MK_VARIANT] != 0;
 #if MK_FIELD == 0
     using F = br::FieldGold;
 #else
     using F = br::FieldDual;
 #endif
-    return br::launch_bootstrap<F, MK_LOGN, NPF, MINB>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out,
-                                                       count, st);
+    return br::launch_bootstrap<F, MK_LOGN, NPF, MINB, TWG>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
+                                                            acc_out, count, st);
 }
 }  // namespace mk

@@ -244,8 +244,6 @@ struct HostNtt32 {
         const uint32_t scale = (uint32_t)(((uint64_t)n_inv << 32) % p);
         for (uint32_t j = 0; j < N; ++j) dst[j] = mulm(a[j], scale, p);
     }
-    // Twiddle with its Shoup companion floor(w * 2^32 / p).
-    static uint32_t shoup_companion(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
 };
 
 template <class F>
@@ -310,7 +308,7 @@ struct mk_ctx {
     int device = -1;
     cudaStream_t stream = nullptr;
     int form = MK_FORM_NTT2;
-    int variant = 3;
+    int variant = 2;
     uint32_t max_batch = 4096;
     std::vector<uint32_t> crs;
     std::vector<PartyKeys> party;
@@ -474,13 +472,14 @@ int ensure_device_keys(mk_ctx *c) {
     } else {
         if (!c->ntt_p1.N && !(c->ntt_p1.init(kP1, N) && c->ntt_p2.init(kP2, N)))
             return fail(c, MK_EPARAMS, "ring dimension not supported by the two-prime NTT");
-        uint32_t *tw = reinterpret_cast<uint32_t *>(h_tw.data());  // [2][N][4]
+        uint32_t *tw = reinterpret_cast<uint32_t *>(h_tw.data());  // [2][N] of {w1, w2, w1', w2'}
+        auto comp = [](uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); };  // Shoup
         for (uint32_t m = 0; m < N; ++m) {
+            uint32_t *ef = tw + 4 * (size_t)m, *ei = tw + 4 * ((size_t)N + m);
             const uint32_t f1 = c->ntt_p1.psi_rev[m], f2 = c->ntt_p2.psi_rev[m];
             const uint32_t i1 = c->ntt_p1.psi_inv_rev[m], i2 = c->ntt_p2.psi_inv_rev[m];
-            uint32_t *ef = tw + 4 * (size_t)m, *ei = tw + 4 * ((size_t)N + m);
-            ef[0] = f1, ef[1] = f2, ef[2] = HostNtt32::shoup_companion(f1, kP1), ef[3] = HostNtt32::shoup_companion(f2, kP2);
-            ei[0] = i1, ei[1] = i2, ei[2] = HostNtt32::shoup_companion(i1, kP1), ei[3] = HostNtt32::shoup_companion(i2, kP2);
+            ef[0] = f1, ef[1] = f2, ef[2] = comp(f1, kP1), ef[3] = comp(f2, kP2);
+            ei[0] = i1, ei[1] = i2, ei[2] = comp(i1, kP1), ei[3] = comp(i2, kP2);
         }
         auto dual = [&](const uint32_t *src, uint64_t *dst, bool negate) {
             std::vector<uint32_t> r1(N), r2(N);

@@ -62,11 +62,14 @@ cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, c
                                     uint32_t count, int64_t max_steps, uint32_t *acc,
                                     cudaStream_t st);
 
-// Blind-rotation variants: digit polynomials per forward transform (1 or 3)
-// and the minimum resident CTAs per SM the register allocation is capped for.
+// Blind-rotation variants: digit polynomials per forward transform (1 or 3),
+// the minimum resident CTAs per SM the register allocation is capped for, and
+// where the twiddles live (0: a shared-memory copy per CTA, 1: global memory
+// through the read-only cache).  All give identical results.
 constexpr int kNumVariants = 4;
-constexpr int kVariantNpf[kNumVariants] = {3, 3, 1, 1};
-constexpr int kVariantMinBlocks[kNumVariants] = {1, 2, 3, 4};
+constexpr int kVariantNpf[kNumVariants] = {3, 1, 3, 3};
+constexpr int kVariantMinBlocks[kNumVariants] = {3, 4, 3, 4};
+constexpr int kVariantTwg[kNumVariants] = {0, 1, 1, 1};
 
 // Per-(ring dimension, variant) blind-rotation launchers, one translation unit
 // each (mk_br.cu built with -DMK_LOGN -DMK_VARIANT).  abar_in == nullptr: the
@@ -79,8 +82,9 @@ constexpr int kVariantMinBlocks[kNumVariants] = {1, 2, 3, 4};
                                                           const uint32_t *ct_b, const uint32_t *abar_in,      \
                                                           int64_t max_steps, uint32_t *ext, uint32_t *acc_out, \
                                                           uint32_t count, cudaStream_t st);
-#define MK_DECLARE_BOOTSTRAP_F(LOGN, F) \
-    MK_DECLARE_BOOTSTRAP(LOGN, F, 0) MK_DECLARE_BOOTSTRAP(LOGN, F, 1) MK_DECLARE_BOOTSTRAP(LOGN, F, 2) MK_DECLARE_BOOTSTRAP(LOGN, F, 3)
+#define MK_DECLARE_BOOTSTRAP_F(LOGN, F)                                                                       \
+    MK_DECLARE_BOOTSTRAP(LOGN, F, 0) MK_DECLARE_BOOTSTRAP(LOGN, F, 1) MK_DECLARE_BOOTSTRAP(LOGN, F, 2)          \
+    MK_DECLARE_BOOTSTRAP(LOGN, F, 3)
 MK_DECLARE_BOOTSTRAP_F(8, 0)
 MK_DECLARE_BOOTSTRAP_F(8, 1)
 MK_DECLARE_BOOTSTRAP_F(10, 0)

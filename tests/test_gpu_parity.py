@@ -210,7 +210,7 @@ def test_toy_every_variant_bit_exact(toy, form, variant):
         assert np.array_equal(from_dev(acc), ref)
     finally:
         ctx.set_form("ntt2")
-        ctx.set_variant(3)
+        ctx.set_variant(2)
 
 
 @pytest.mark.parametrize("form,variant", FORM_VARIANTS)
@@ -233,7 +233,7 @@ def test_full_k2_every_variant_sampled(full2, form, variant):
         got = from_dev(out)
     finally:
         ctx.set_form("ntt2")
-        ctx.set_variant(3)
+        ctx.set_variant(2)
     exp = np.array([TRUTH[int(t)](int(x), int(y)) for t, x, y in zip(types, b1, b2)], np.uint8)
     assert np.array_equal(o.decrypt(P, keys, got), exp)
     idx = np.array([0, 50, 95])
