@@ -121,14 +121,26 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- roofline bookkeeping
-def modmuls_per_cmux(P, form="ntt"):
-    """Modular multiplies of one CMux step: (k+2)(d+1) length-N transforms of
-    (N/2) log2 N butterflies, plus (2k+4) d N pointwise products (hybrid
-    product, phase A and B); once per prime (the two-prime form has two)."""
+def work_per_cmux(P, form="ntt"):
+    """Algorithmic work of one CMux step, in the unit of the form's ceiling.
+    NTT forms: modular multiplies -- (k+2)(d+1) length-N transforms of
+    (N/2) log2 N butterflies plus (2k+4) d N pointwise products (hybrid
+    product, phase A and B), once per prime.  FFT form: FP64 instructions
+    (an FMA counts one) -- 8 per complex butterfly, 4 per complex twist of
+    each transformed point and 4 per pointwise complex multiply-add, on
+    M = N/2 folded points."""
     k, d, N = P["k"], P["d"], P["N"]
     logn = N.bit_length() - 1
+    if form == "fft":
+        M = N // 2
+        return (k + 2) * (d + 1) * ((M // 2) * (logn - 1) * 8 + M * 4) + (2 * k + 4) * d * M * 4
     per_prime = (k + 2) * (d + 1) * (N // 2) * logn + (2 * k + 4) * d * N
     return per_prime * (2 if form == "ntt2" else 1)
+
+
+# Work units per measured butterfly of the ceiling microbenchmark.
+UNITS_PER_BUTTERFLY = {"ntt": 1, "ntt2": 1, "fft": 8}
+UNIT_NAME = {"ntt": "G modmul/s", "ntt2": "G modmul/s", "fft": "G FP64 instr/s"}
 
 
 def kernel_source_hash():
@@ -291,16 +303,20 @@ def run_ours(args):
 
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
-    mm_per_gate = modmuls_per_cmux(P, args.form) * P["k"] * P["n"]
-    achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / 1e9  # G modmul/s
-    peak = B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / 1e9
+    mm_per_gate = work_per_cmux(P, args.form) * P["k"] * P["n"]
+    achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / 1e9
+    peak = (B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / 1e9
+            * UNITS_PER_BUTTERFLY[args.form])
     traffic_pg = ncu_traffic_per_gate()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G modmul/s",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT_NAME[args.form],
                 "frac": achieved / peak, "traffic": (traffic_pg * G if traffic_pg is not None else None),
-                "kernel": "bootstrap_ntt_kernel<%s, 10, variant %d>" % (args.form, variant), "algorithmic_modmuls_per_gate": mm_per_gate,
+                "kernel": "bootstrap_ntt_kernel<%s, 10, variant %d>" % (args.form, variant),
+                "algorithmic_work_per_gate": mm_per_gate,
                 "peak_source": ("measured: register-resident butterfly loop of the same arithmetic on every SM "
-                                "(mk_measure_butterfly_rate, %s), one modular multiply per butterfly"
-                                % {"ntt": "Goldilocks 64-bit", "ntt2": "Harvey/Shoup mod a 30-bit prime"}[args.form]),
+                                "(mk_measure_butterfly_rate, %s)"
+                                % {"ntt": "Goldilocks 64-bit, one modmul per butterfly",
+                                   "ntt2": "Harvey/Shoup mod a 30-bit prime, one modmul per butterfly",
+                                   "fft": "complex FP64, 8 FP64 instructions per butterfly"}[args.form]),
                 "br_share_of_step": br_ms / total_ms if total_ms else None}
 
     ctx.close()
@@ -315,7 +331,8 @@ def run_ours(args):
                    "bg_bit": P["bg_bit"], "d": P["d"], "ks_bit": P["ks_bit"], "t": P["t"],
                    "sigma_lwe": P["sigma_lwe"], "sigma_rlwe": P["sigma_rlwe"],
                    "form": {"ntt": "ntt64 (exact, Goldilocks prime)",
-                            "ntt2": "ntt2x30 (exact, two 30-bit primes + CRT)"}[args.form],
+                            "ntt2": "ntt2x30 (exact, two 30-bit primes + CRT)",
+                            "fft": "fft64 (FP64, rounded; approximate)"}[args.form],
                    "variant": variant, "autotune_ms": variant_ms,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "no flush: per-step working set (BK 82 MB NTT domain + KS 110 MB + 37 MB "
@@ -412,7 +429,7 @@ def main():
     ap.add_argument("--k4-gates", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--autotune-gates", type=int, default=2048)
-    ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2"])
+    ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2", "fft"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -84,13 +84,18 @@ int mk_ctx_destroy(mk_ctx *ctx);
 int mk_ctx_set_stream(mk_ctx *ctx, void *stream);
 int mk_ctx_get_params(const mk_ctx *ctx, mk_params *out);
 
-/* Negacyclic-product form used by the blind rotation.  Both are exact (the
- * product sums are recovered as integers and reduced mod 2^32), so both give
- * bit-identical ciphertexts.  Changing the form rebuilds the device keys on
- * the next gate call.  Default: MK_FORM_NTT2. */
+/* Negacyclic-product form used by the blind rotation.  The two NTT forms are
+ * exact (the product sums are recovered as integers and reduced mod 2^32),
+ * so they give bit-identical ciphertexts.  The FP64 FFT form rounds each
+ * product to the nearest integer; its error per product is small (well
+ * below 2^12 torus32 units) but not zero, so its ciphertexts differ from the
+ * exact ones in low bits and, rarely, more (a flipped gadget digit), while
+ * decrypting to the same bits.  Changing the form rebuilds the device keys
+ * on the next gate call.  Default: MK_FORM_NTT2. */
 enum {
-    MK_FORM_NTT = 0, /* NTT over the prime 2^64 - 2^32 + 1 */
-    MK_FORM_NTT2 = 1 /* NTTs over the primes 0x3fff4001 and 0x3ffee001, CRT */
+    MK_FORM_NTT = 0,  /* NTT over the prime 2^64 - 2^32 + 1 */
+    MK_FORM_NTT2 = 1, /* NTTs over the primes 0x3fff4001 and 0x3ffee001, CRT */
+    MK_FORM_FFT = 2   /* FP64 FFT of N/2 folded complex points */
 };
 int mk_ctx_set_form(mk_ctx *ctx, int form);
 int mk_ctx_get_form(const mk_ctx *ctx, int *form);
@@ -290,7 +295,9 @@ int mk_timing_read(mk_ctx *ctx, int kernel, double *ms_total, uint64_t *launches
  * butterflies on every SM of `device`; *per_s receives butterflies per
  * second.  form = MK_FORM_NTT: Goldilocks butterflies (one 64-bit modular
  * multiply, add and subtract); MK_FORM_NTT2: Harvey butterflies modulo a
- * 30-bit prime (one Shoup multiply, one conditional subtraction, add, sub).
+ * 30-bit prime (one Shoup multiply, one conditional subtraction, add, sub);
+ * MK_FORM_FFT: complex FP64 butterflies (one complex multiply, two complex
+ * additions).
  * No paper counterpart: a measurement aid for the roofline of the blind
  * rotation. */
 int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters, double *per_s);

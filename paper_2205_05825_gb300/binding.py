@@ -18,7 +18,7 @@ ERRORS = {-1: "MK_EINVAL", -2: "MK_ENOMEM", -3: "MK_EPARAMS", -4: "MK_ETIMEOUT",
 GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
 PRESETS = {"toy": 0, "full": 1, "paper": 2}
 NUM_VARIANTS = 4
-FORMS = {"ntt": 0, "ntt2": 1}
+FORMS = {"ntt": 0, "ntt2": 1, "fft": 2}
 
 U32P = ctypes.POINTER(ctypes.c_uint32)
 U8P = ctypes.POINTER(ctypes.c_uint8)

@@ -22,9 +22,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu"]
 # mk_br.cu is compiled once per (log2 N, blind-rotation variant).
 BR_SOURCE = "mk_br.cu"
-BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(4)]
+BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(4)] + \
+    [(logn, 2, 0) for logn in (8, 10)]
 CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp"]
-HEADERS = ["mk_internal.h", "mk_bootstrap.cuh", BR_SOURCE]
+HEADERS = ["mk_internal.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", BR_SOURCE]
 
 
 def _newest_input():

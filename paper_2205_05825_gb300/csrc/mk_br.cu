@@ -1,8 +1,10 @@
 // Blind-rotation instantiation for one (ring dimension, field, variant),
 // chosen by the build with -DMK_LOGN=<log2 N> -DMK_FIELD=<0|1>
 // -DMK_VARIANT=<v>; field 0 = Goldilocks (MK_FORM_NTT), 1 = two 30-bit primes
-// (MK_FORM_NTT2); the variant table is in mk_internal.h.
+// (MK_FORM_NTT2), 2 = FP64 FFT (MK_FORM_FFT, one variant); the variant table
+// is in mk_internal.h.
 #include "mk_bootstrap.cuh"
+#include "mk_bootstrap_fft.cuh"
 
 #ifndef MK_LOGN
 #error "compile with -DMK_LOGN=<log2 N> -DMK_VARIANT=<v>"
@@ -20,6 +22,13 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
     constexpr int NPF = kVariantNpf[MK_VARIANT];
     constexpr int MINB = kVariantMinBlocks[MK_VARIANT];
     constexpr bool TWG = kVariantTwg[MK_VARIANT] != 0;
+#if MK_FIELD == 2
+    (void)NPF;
+    (void)MINB;
+    (void)TWG;
+    return br::launch_bootstrap_fft<MK_LOGN - 1>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
+                                                 st);
+#else
 #if MK_FIELD == 0
     using F = br::FieldGold;
 #else
@@ -27,5 +36,6 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
 #endif
     return br::launch_bootstrap<F, MK_LOGN, NPF, MINB, TWG>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
                                                             acc_out, count, st);
+#endif
 }
 }  // namespace mk

@@ -4,6 +4,7 @@
 // kernels, and the C ABI declared in include/mk_tfhe.h.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -246,6 +247,62 @@ struct HostNtt32 {
     }
 };
 
+// Host side of the FP64 FFT form: negacyclic transform of size M = N/2 over C
+// (Cooley-Tukey with psi = exp(i pi / M) in bit-reversed powers), after folding
+// (c_j + i c_{j+M}) and twisting by theta^j = exp(-i pi j / N).
+struct HostFft {
+    uint32_t N = 0, M = 0, logM = 0;
+    std::vector<std::complex<double>> psi_rev, psi_inv_rev, theta;
+    void init(uint32_t n_) {
+        N = n_;
+        M = N / 2;
+        logM = 0;
+        while ((1u << logM) < M) ++logM;
+        psi_rev.resize(M);
+        psi_inv_rev.resize(M);
+        theta.resize(M);
+        const double pi = 3.14159265358979323846;
+        for (uint32_t m = 0; m < M; ++m) {
+            uint32_t r = 0;
+            for (uint32_t b = 0; b < logM; ++b)
+                if (m & (1u << b)) r |= 1u << (logM - 1 - b);
+            psi_rev[m] = std::polar(1.0, pi * r / M);
+            psi_inv_rev[m] = std::conj(psi_rev[m]);
+            theta[m] = std::polar(1.0, -pi * m / N);
+        }
+    }
+    void forward(std::complex<double> *a) const {
+        uint32_t t = M;
+        for (uint32_t m = 1; m < M; m <<= 1) {
+            t >>= 1;
+            for (uint32_t i = 0; i < m; ++i) {
+                const uint32_t j1 = 2 * i * t;
+                const std::complex<double> S = psi_rev[m + i];
+                for (uint32_t j = j1; j < j1 + t; ++j) {
+                    const std::complex<double> U = a[j], V = a[j + t] * S;
+                    a[j] = U + V;
+                    a[j + t] = U - V;
+                }
+            }
+        }
+    }
+    // Device form of a key polynomial: fold, twist, transform, times 1/M;
+    // coefficients taken as signed 32-bit integers (same value mod 2^32).
+    void to_device(const uint32_t *src, double *dst, bool negate) const {
+        std::vector<std::complex<double>> z(M);
+        for (uint32_t j = 0; j < M; ++j) {
+            double lo = (double)(int32_t)src[j], hi = (double)(int32_t)src[j + M];
+            if (negate) lo = -lo, hi = -hi;
+            z[j] = std::complex<double>(lo, hi) * theta[j];
+        }
+        forward(z.data());
+        for (uint32_t j = 0; j < M; ++j) {
+            dst[2 * j] = z[j].real() / M;
+            dst[2 * j + 1] = z[j].imag() / M;
+        }
+    }
+};
+
 template <class F>
 void parallel_for(size_t count, F &&fn) {
     unsigned nt = std::thread::hardware_concurrency();
@@ -314,6 +371,7 @@ struct mk_ctx {
     std::vector<PartyKeys> party;
     HostNtt ntt;
     HostNtt32 ntt_p1, ntt_p2;
+    HostFft fft;
     // device state
     bool dev_keys_valid = false;
     void *d_tw = nullptr;       // [2][N] twiddles (8 or 16 bytes each)
@@ -339,8 +397,8 @@ struct mk_ctx {
         return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form};
     }
     DeviceKeys dkeys() const {
-        // twiddles: [2][N] of 8-byte (NTT) or 16-byte (NTT2) entries
-        const size_t half = (form == MK_FORM_NTT2 ? 16 : 8) * (size_t)P.N;
+        // twiddles: [2][N] of 8-byte (NTT) or 16-byte (NTT2) entries; FFT: one [3][N/2] table
+        const size_t half = (form == MK_FORM_NTT2 ? 16 : (form == MK_FORM_FFT ? 0 : 8)) * (size_t)P.N;
         return DeviceKeys{d_tw, (const unsigned char *)d_tw + half, d_bk, d_keyA, d_ks};
     }
 };
@@ -450,8 +508,10 @@ int ensure_device_keys(mk_ctx *c) {
     const size_t bk_entries = (size_t)k * n * 3 * d;  // polynomials
     const size_t keyA_entries = (size_t)(k + 1) * d;
     // Both forms store 8 bytes per NTT-domain coefficient.
+    // 8 bytes per NTT-domain coefficient (NTT forms) or per folded coefficient
+    // pair half (FFT form: N/2 double2 = 8 N bytes): the same sizes.
     std::vector<uint64_t> h_bk(bk_entries * N), h_keyA(keyA_entries * N);
-    std::vector<unsigned char> h_tw(2 * (size_t)N * 16);
+    std::vector<unsigned char> h_tw(2 * (size_t)N * 16);  // the largest twiddle table of the forms
     // src polynomial of BK entry e and of keyA entry r (negated for the CRS)
     auto bk_src = [&](size_t e) {
         const uint32_t i = (uint32_t)(e / ((size_t)n * 3 * d));
@@ -469,6 +529,20 @@ int ensure_device_keys(mk_ctx *c) {
         }
         parallel_for(bk_entries, [&](size_t e) { c->ntt.to_ntt(bk_src(e), h_bk.data() + e * N, false, true); });
         for (size_t r = 0; r < keyA_entries; ++r) c->ntt.to_ntt(keyA_src(r), h_keyA.data() + r * N, r < d, true);
+    } else if (c->form == MK_FORM_FFT) {
+        if (!c->fft.N) c->fft.init(N);
+        const uint32_t M = N / 2;
+        double *tw = reinterpret_cast<double *>(h_tw.data());  // [3][M] double2: forward, inverse, twist
+        for (uint32_t m = 0; m < M; ++m) {
+            tw[2 * m] = c->fft.psi_rev[m].real(), tw[2 * m + 1] = c->fft.psi_rev[m].imag();
+            tw[2 * (M + m)] = c->fft.psi_inv_rev[m].real(), tw[2 * (M + m) + 1] = c->fft.psi_inv_rev[m].imag();
+            tw[2 * (2 * M + m)] = c->fft.theta[m].real(), tw[2 * (2 * M + m) + 1] = c->fft.theta[m].imag();
+        }
+        parallel_for(bk_entries, [&](size_t e) {
+            c->fft.to_device(bk_src(e), reinterpret_cast<double *>(h_bk.data() + e * N), false);
+        });
+        for (size_t r = 0; r < keyA_entries; ++r)
+            c->fft.to_device(keyA_src(r), reinterpret_cast<double *>(h_keyA.data() + r * N), r < d);
     } else {
         if (!c->ntt_p1.N && !(c->ntt_p1.init(kP1, N) && c->ntt_p2.init(kP2, N)))
             return fail(c, MK_EPARAMS, "ring dimension not supported by the two-prime NTT");
@@ -748,7 +822,8 @@ int mk_ctx_get_params(const mk_ctx *c, mk_params *out) {
 
 int mk_ctx_set_form(mk_ctx *c, int form) {
     if (!c) return MK_EINVAL;
-    if (form != MK_FORM_NTT && form != MK_FORM_NTT2) return fail(c, MK_EINVAL, "unknown product form");
+    if (form != MK_FORM_NTT && form != MK_FORM_NTT2 && form != MK_FORM_FFT)
+        return fail(c, MK_EINVAL, "unknown product form");
     if (form != c->form) c->dev_keys_valid = false;  // the NTT-domain keys are rebuilt on next use
     c->form = form;
     return MK_OK;
@@ -1379,7 +1454,8 @@ int mk_timing_read(mk_ctx *c, int kernel, double *ms_total, uint64_t *launches) 
 }
 
 int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters, double *per_s) {
-    if (!per_s || iters == 0 || (form != MK_FORM_NTT && form != MK_FORM_NTT2)) return MK_EINVAL;
+    if (!per_s || iters == 0 || (form != MK_FORM_NTT && form != MK_FORM_NTT2 && form != MK_FORM_FFT))
+        return MK_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return MK_EDEVICE;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return MK_EDEVICE;
@@ -1392,8 +1468,9 @@ int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters
     cudaEventCreate(&b);
     int rc = MK_OK;
     auto launch = [&](uint32_t it) {
-        return form == MK_FORM_NTT ? launch_butterfly_peak(blocks, threads, it, sink, st)
-                                   : launch_butterfly_peak2(blocks, threads, it, reinterpret_cast<uint32_t *>(sink), st);
+        if (form == MK_FORM_NTT) return launch_butterfly_peak(blocks, threads, it, sink, st);
+        if (form == MK_FORM_FFT) return launch_butterfly_peak_fft(blocks, threads, it, reinterpret_cast<double *>(sink), st);
+        return launch_butterfly_peak2(blocks, threads, it, reinterpret_cast<uint32_t *>(sink), st);
     };
     if (launch(iters / 8 + 1) != cudaSuccess) rc = MK_EDEVICE;  // warm-up
     cudaEventRecord(a, st);

@@ -29,11 +29,12 @@ struct GateDesc {
 
 // Device-resident key material of one context, in the layouts the kernels read.
 // Element type of the NTT-domain arrays by form: MK_FORM_NTT uint64 (mod
-// Goldilocks); MK_FORM_NTT2 uint2 (residues mod kP1, kP2, Montgomery form).
+// Goldilocks); MK_FORM_NTT2 uint2 (residues mod kP1, kP2, Montgomery form);
+// MK_FORM_FFT double2 (N/2 folded complex points, times 2/N).
 // Twiddle entries: uint64 (NTT) or uint4 {w1, w2, w1', w2'} with Shoup
 // companions w' = floor(w * 2^32 / p) (NTT2).
 struct DeviceKeys {
-    const void *tw_fwd;   // [N] psi^bitrev(m)
+    const void *tw_fwd;   // [N] psi^bitrev(m); FFT form: [3][N/2] forward, inverse, twist
     const void *tw_inv;   // [N] psi^-bitrev(m)
     const void *bk;       // [k][n][3][d][N] NTT domain, bit-reversed order, times N^-1
     const void *keyA;     // [(k+1)][d][N]: [0] = NTT(-a), [j] = NTT(pk_j), times N^-1
@@ -89,6 +90,8 @@ MK_DECLARE_BOOTSTRAP_F(8, 0)
 MK_DECLARE_BOOTSTRAP_F(8, 1)
 MK_DECLARE_BOOTSTRAP_F(10, 0)
 MK_DECLARE_BOOTSTRAP_F(10, 1)
+MK_DECLARE_BOOTSTRAP(8, 2, 0)
+MK_DECLARE_BOOTSTRAP(10, 2, 0)
 
 // a9: per-party key switch of ext [count][k*N+1] into out rows desc[g].out
 // (or row g when desc == nullptr).
@@ -139,5 +142,8 @@ cudaError_t launch_butterfly_peak(uint32_t blocks, uint32_t threads, uint32_t it
 // Same for Harvey/Shoup butterflies modulo a 30-bit prime (MK_FORM_NTT2).
 cudaError_t launch_butterfly_peak2(uint32_t blocks, uint32_t threads, uint32_t iters, uint32_t *sink,
                                    cudaStream_t st);
+// Same for complex FP64 butterflies (MK_FORM_FFT).
+cudaError_t launch_butterfly_peak_fft(uint32_t blocks, uint32_t threads, uint32_t iters, double *sink,
+                                      cudaStream_t st);
 
 }  // namespace mk

@@ -199,7 +199,43 @@ __global__ void butterfly_peak2_kernel(uint32_t iters, uint32_t *sink) {
     if (r == 0x1234567u) sink[blockIdx.x] = r;  // keeps the loop live; practically never stores
 }
 
+// Independent complex FP64 butterflies (one complex multiply, two complex
+// additions): the inner operation of MK_FORM_FFT.
+__global__ void butterfly_peak_fft_kernel(uint32_t iters, double *sink) {
+    double xr[8], xi[8], yr[8], yi[8];
+    double wr = 0.7071067811865476 + 1e-9 * threadIdx.x, wi = 0.7071067811865475;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        xr[c] = 1.0 + c + blockIdx.x;
+        xi[c] = 0.5 * c;
+        yr[c] = 2.0 - c;
+        yi[c] = 0.25 + threadIdx.x;
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const double vr = fma(yr[c], wr, -yi[c] * wi), vi = fma(yr[c], wi, yi[c] * wr);
+            const double ur = xr[c], ui = xi[c];
+            xr[c] = ur + vr;
+            xi[c] = ui + vi;
+            yr[c] = ur - vr;
+            yi[c] = ui - vi;
+        }
+        wr = fma(wr, 0.9999999, 1e-12);
+    }
+    double r = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) r += xr[c] + xi[c] + yr[c] + yi[c];
+    if (r == 1.2345) sink[blockIdx.x] = r;  // keeps the loop live; practically never stores
+}
+
 }  // namespace
+
+cudaError_t launch_butterfly_peak_fft(uint32_t blocks, uint32_t threads, uint32_t iters, double *sink,
+                                      cudaStream_t st) {
+    butterfly_peak_fft_kernel<<<blocks, threads, 0, st>>>(iters, sink);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_butterfly_peak2(uint32_t blocks, uint32_t threads, uint32_t iters, uint32_t *sink,
                                    cudaStream_t st) {
@@ -241,6 +277,11 @@ BootstrapFn pick(const LaunchShape &S) {
     static const BootstrapFn t8[2][kNumVariants] = {MK_ROW(8, 0), MK_ROW(8, 1)};
     static const BootstrapFn t10[2][kNumVariants] = {MK_ROW(10, 0), MK_ROW(10, 1)};
 #undef MK_ROW
+    if (S.form == MK_FORM_FFT) {  // one kernel for every variant number
+        if (S.logN == 8) return launch_bootstrap_logn8_f2_v0;
+        if (S.logN == 10) return launch_bootstrap_logn10_f2_v0;
+        return nullptr;
+    }
     if (S.variant < 0 || S.variant >= kNumVariants || S.form < 0 || S.form > 1) return nullptr;
     if (S.logN == 8) return t8[S.form][S.variant];
     if (S.logN == 10) return t10[S.form][S.variant];
