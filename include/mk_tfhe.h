@@ -234,6 +234,35 @@ typedef struct mk_gate_rec {
 int mk_circuit_netlist(int op, uint32_t kbits, mk_gate_rec *gates, uint32_t gate_cap, uint32_t *n_gates,
                        int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs, uint32_t *n_levels);
 
+/* ---------------------------------------------------------------- serving */
+/* Continuous batching of operator requests from several clients (the paper's
+ * cloud server evaluating participants' circuits, Sec. 4.5).  Every admitted
+ * request keeps its wire ciphertexts in one device pool of `pool_rows`
+ * ciphertext rows; mk_server_step runs one wave: one batched bootstrap +
+ * key-switch launch over at most `wave_gates` ready gates of all running
+ * requests (each contributes the gates of its current netlist level; a level
+ * is split across waves when it does not fit), after admitting queued
+ * requests, in arrival order, while the pool has room.  Requests therefore
+ * join while others are on the GPU, and their gates share launches.  Results
+ * are the same alone and in any mix (every gate touches only its own
+ * request's wires; the NTT forms are exact).
+ *
+ * mk_server_submit queues a request: operator MK_OP_*, kbits, pairs and the
+ * operand/output device buffers of mk_*_kbit (d_out2 = remainder for
+ * MK_OP_DIV, NULL otherwise).  The operands must stay valid until the request
+ * is running, the outputs are written when it is done.  mk_server_step
+ * synchronises the context's stream before returning; *n_done = requests
+ * finished by this wave.  mk_server_poll: *state = 0 queued, 1 running,
+ * 2 done. */
+typedef struct mk_server mk_server;
+int mk_server_create(mk_ctx *ctx, uint32_t wave_gates, uint64_t pool_rows, mk_server **out);
+int mk_server_destroy(mk_server *srv);
+int mk_server_submit(mk_server *srv, int op, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b,
+                     uint32_t *d_out, uint32_t *d_out2, uint32_t pairs, uint64_t *ticket);
+int mk_server_step(mk_server *srv, uint32_t *n_done);
+int mk_server_poll(const mk_server *srv, uint64_t ticket, int *state);
+int mk_server_stats(const mk_server *srv, uint64_t *waves, uint64_t *gates, uint32_t *running, uint32_t *queued);
+
 /* ---------------------------------------------------------------- stages */
 /* The stages of one bootstrapped gate, for stage-by-stage comparison.
  * mk_stage_modswitch: d_abar[g] = mod-switched words of lin(...) with the

@@ -92,6 +92,14 @@ _SIGS = {
     "mk_circuit_netlist": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, VP, ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32), VP, ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
+    "mk_server_create": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(VP)]),
+    "mk_server_destroy": (ctypes.c_int, [VP]),
+    "mk_server_submit": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_uint32, VP, VP, VP, VP, ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "mk_server_step": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_uint32)]),
+    "mk_server_poll": (ctypes.c_int, [VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "mk_server_stats": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "mk_timing_enable": (ctypes.c_int, [VP, ctypes.c_int]),
     "mk_timing_reset": (ctypes.c_int, [VP]),
     "mk_timing_read": (ctypes.c_int, [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -435,3 +443,53 @@ def circuit_netlist(op, kbits):
         raise MkError("mk_circuit_netlist: %s" % ERRORS.get(rc, rc))
     return dict(ka=kbits, kb=kbits, gates=[(g.op, g.a, g.neg_a, g.b, g.neg_b) for g in gates[:ng.value]],
                 outputs=[(o >> 1, o & 1) for o in outs[:no.value]], levels=nl.value)
+
+
+class Server:
+    """mk_server: continuous batching of operator requests on one context."""
+
+    def __init__(self, ctx, wave_gates=4096, pool_rows=1 << 18):
+        self.ctx = ctx
+        h = VP()
+        ctx._check(ctx.L.mk_server_create(ctx.h, wave_gates, pool_rows, ctypes.byref(h)), "mk_server_create")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            self.ctx.L.mk_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, op, kbits, a, b, out, out2=None):
+        """a, b: CUDA tensors [pairs][kbits][W]; out (and out2 for div) receive the result."""
+        t = ctypes.c_uint64()
+        pairs = a.numel() // (kbits * self.ctx.W)
+        opi = OPS[op] if isinstance(op, str) else int(op)
+        self.ctx._check(self.ctx.L.mk_server_submit(self.h, opi, kbits, _dptr(a), _dptr(b), _dptr(out),
+                                                    _dptr(out2) if out2 is not None else None, pairs,
+                                                    ctypes.byref(t)), "mk_server_submit")
+        self._keep[t.value] = (a, b, out, out2)
+        return t.value
+
+    def step(self):
+        n = ctypes.c_uint32()
+        self.ctx._check(self.ctx.L.mk_server_step(self.h, ctypes.byref(n)), "mk_server_step")
+        return n.value
+
+    def poll(self, ticket):
+        st = ctypes.c_int()
+        self.ctx._check(self.ctx.L.mk_server_poll(self.h, ticket, ctypes.byref(st)), "mk_server_poll")
+        return st.value
+
+    def stats(self):
+        w, g = ctypes.c_uint64(), ctypes.c_uint64()
+        r, q = ctypes.c_uint32(), ctypes.c_uint32()
+        self.ctx._check(self.ctx.L.mk_server_stats(self.h, ctypes.byref(w), ctypes.byref(g), ctypes.byref(r),
+                                                   ctypes.byref(q)), "mk_server_stats")
+        return dict(waves=w.value, gates=g.value, running=r.value, queued=q.value)

@@ -24,8 +24,8 @@ CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu"]
 BR_SOURCE = "mk_br.cu"
 BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(4)] + \
     [(logn, 2, 0) for logn in (8, 10)]
-CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp"]
-HEADERS = ["mk_internal.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", BR_SOURCE]
+CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp", "mk_server.cpp"]
+HEADERS = ["mk_internal.h", "mk_ctx.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", BR_SOURCE]
 
 
 def _newest_input():

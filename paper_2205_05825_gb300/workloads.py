@@ -109,3 +109,72 @@ def bits_to_int(bits):
 
 def encryption_seed(config_id, party, stream=0):
     return INPUT_SEED_BASE + (config_id << 12) + (party << 4) + stream
+
+
+# ----------------------------------------------------------------------------- serving (regression requests)
+def wrap_int(v, bits=16):
+    """Two's-complement wrap of Python/numpy integers to `bits` bits."""
+    v = np.asarray(v, np.int64) % (1 << bits)
+    return np.where(v >= 1 << (bits - 1), v - (1 << bits), v)
+
+
+def regression_data(samples=64, features=4, config_id=5):
+    """Synthetic linear-regression data (the paper's is unpublished): integer
+    features uniform in [-16, 16], integer weights, y = w.x + noise in [-2, 2]."""
+    r = rng(config_id)
+    X = r.integers(-16, 17, size=(samples, features)).astype(np.int64)
+    w = r.integers(-4, 5, size=features).astype(np.int64)
+    y = X @ w + r.integers(-2, 3, size=samples)
+    return X, w, y
+
+
+def gd_request_stream(count, bits=16, config_id=5):
+    """`count` single-operation requests (op, a, b) drawn from one integer
+    gradient-descent step on regression_data, in the step's own proportions:
+    products x*w and err*x (mul), partial sums and gradient sums (add),
+    residuals (sub) and the per-feature scaling of the gradient (div)."""
+    X, w, y = regression_data(config_id=config_id)
+    m, f = X.shape
+    ops = []
+    for i in range(m):
+        acc = 0
+        for j in range(f):
+            ops.append(("mul", int(X[i, j]), int(w[j])))
+            if j:
+                ops.append(("add", int(acc), int(X[i, j] * w[j])))
+            acc += int(X[i, j] * w[j])
+        ops.append(("sub", int(acc), int(y[i])))
+        err = acc - int(y[i])
+        for j in range(f):
+            ops.append(("mul", int(err), int(X[i, j])))
+    for j in range(f):
+        grad = int((X @ w - y) @ X[:, j])
+        ops.append(("div", grad, m))
+    r = rng(config_id * 7 + 1)
+    pick = r.choice(len(ops), size=count, replace=count > len(ops))
+    out = []
+    for k_ in pick:
+        op, a, b = ops[k_]
+        a, b = int(wrap_int(a, bits)), int(wrap_int(b, bits))
+        if op == "div" and b == 0:
+            b = 1
+        out.append((op, a, b))
+    return out
+
+
+def expected_result(op, a, b, bits=16):
+    """Native two's-complement result of one request (q, r for div)."""
+    if op == "add":
+        return int(wrap_int(a + b, bits))
+    if op == "sub":
+        return int(wrap_int(a - b, bits))
+    if op == "mul":
+        return int(a * b)
+    q = int(np.trunc(a / b))
+    return q, a - q * b
+
+
+def poisson_arrivals(count, rate, config_id=5):
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    r = rng(config_id * 13 + 2)
+    return np.cumsum(r.exponential(1.0 / rate, size=count))
