@@ -183,14 +183,21 @@ def run_ours(args):
     B.load(build_if_missing=True)
 
     def setup(k, G):
+        """k = 2: c1 by party 0, c2 by party 1 (every CMux step active).  k > 2:
+        joint-key inputs (every party block non-zero, as for the outputs of
+        earlier gates inside a circuit), so all k*n CMux steps run."""
         P = W.full_params(k)
         ctx = B.Context(P, W.CRS_SEED, device=dev_index)
         for i, s in enumerate(W.party_seeds(k)):
             ctx.keygen(i, s)
         cfg = shard_seed(2, rank)
         types, b1, b2 = W.random_gates(G, config_id=cfg)
-        c1 = ctx.encrypt(0, b1, W.encryption_seed(cfg, 0))
-        c2 = ctx.encrypt(1, b2, W.encryption_seed(cfg, 1))
+        if k == 2:
+            c1 = ctx.encrypt(0, b1, W.encryption_seed(cfg, 0))
+            c2 = ctx.encrypt(1, b2, W.encryption_seed(cfg, 1))
+        else:
+            c1 = ctx.encrypt_joint(b1, W.encryption_seed(cfg, 0))
+            c2 = ctx.encrypt_joint(b2, W.encryption_seed(cfg, 1))
         truth = np.array([[a & b, a | b, 1 - (a & b), 1 - (a | b), a ^ b, 1 - (a ^ b)][t]
                           for t, a, b in zip(types, b1.astype(int), b2.astype(int))], np.uint8)
         return P, ctx, types, c1, c2, truth
@@ -298,8 +305,42 @@ def run_ours(args):
         k4_ms = q0.elapsed_time(q1)
         k4_ok = bool(np.array_equal(ctx4.decrypt(do4), tr4))
         k4 = {"gates_per_s": args.k4_gates / (k4_ms * 1e-3), "gates": args.k4_gates, "ms_per_batch": k4_ms,
-              "decrypt_ok": k4_ok, "active_cmux_steps_per_gate": 2 * P4["n"]}
+              "decrypt_ok": k4_ok, "active_cmux_steps_per_gate": 4 * P4["n"], "inputs": "joint-key"}
         ctx4.close()
+
+    # precision sweep: gates/s of every product form at 2, 4 and 8 parties
+    sweep = None
+    if args.sweep:
+        sweep = []
+        for kk in (2, 4, 8):
+            Pk = W.full_params(kk)
+            ck = B.Context(Pk, W.CRS_SEED, device=dev_index)
+            for i, s_ in enumerate(W.party_seeds(kk)):
+                ck.keygen(i, s_)
+            Gs = 8192
+            ts, x1, x2 = W.random_gates(Gs, config_id=40 + kk)
+            e1 = ck.encrypt_joint(x1, W.encryption_seed(40 + kk, 0))
+            e2 = ck.encrypt_joint(x2, W.encryption_seed(40 + kk, 1))
+            tr = np.array([[a & b, a | b, 1 - (a & b), 1 - (a | b), a ^ b, 1 - (a ^ b)][t]
+                           for t, a, b in zip(ts, x1.astype(int), x2.astype(int))], np.uint8)
+            dt_, d1, d2 = tdev(ts.astype(np.uint8)), tdev(e1), tdev(e2)
+            do = torch.zeros((Gs, ck.W), dtype=torch.int32, device="cuda")
+            for form in ("ntt", "ntt2", "fft"):
+                ck.set_form(form)
+                ck.autotune(1024)
+                ck.gates(dt_, d1, d2, do)
+                torch.cuda.synchronize()
+                s0 = torch.cuda.Event(enable_timing=True)
+                s1 = torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                ck.gates(dt_, d1, d2, do)
+                s1.record(stream)
+                torch.cuda.synchronize()
+                ms = s0.elapsed_time(s1)
+                sweep.append({"parties": kk, "form": form, "gates": Gs, "gates_per_s": Gs / (ms * 1e-3),
+                              "decrypt_ok": bool(np.array_equal(ck.decrypt(do), tr)),
+                              "active_cmux_steps_per_gate": kk * Pk["n"]})
+            ck.close()
 
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
@@ -343,6 +384,7 @@ def run_ours(args):
                                       "latency_ms": plain_ms / plain_g,
                                       "batched_over_plain": value / world / plain_rate},
         "k4": k4,
+        "precision_sweep": sweep,
         "decrypt_ok": bool(ok),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(G + 2 * G * ctx.W * 4),
@@ -430,6 +472,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--autotune-gates", type=int, default=2048)
     ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2", "fft"])
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time every product form at 2, 4 and 8 parties (8192 joint-key gates each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
