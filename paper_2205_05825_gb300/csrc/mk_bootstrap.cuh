@@ -356,7 +356,8 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
     L.twf = 0;
     L.twi = L.twf + tw_bytes;
     L.xbuf = L.twi + tw_bytes;
-    L.acc = L.xbuf + sizeof(E) * NPF * (N + N / 16);
+    // exchange buffer for NPF forward or 2 inverse transforms at once
+    L.acc = L.xbuf + sizeof(E) * (NPF > 2 ? NPF : 2) * (N + N / 16);
     L.abar = L.acc + sizeof(uint32_t) * (k + 1) * N;
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
     return L;
@@ -436,24 +437,43 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
                 }
             }
         }
-        // Inverse transforms due after this slot, one call site for all:
-        //   kind 0: c'_jj -> ACC_jj   (2 <= q <= k)
-        //   kind 1: v -> registers    (q == k)
-        //   kind 2: c'_0 -> ACC_0, kind 3: c'_i -> ACC_i  (q == k+1)
-        const int first = (q >= 2 && q <= k) ? 0 : (q == k ? 1 : (q == k + 1 ? 2 : 4));
-        const int last = (q == k) ? 1 : (q == k + 1 ? 3 : (q >= 2 ? 0 : -1));
-#pragma unroll 1
-        for (int kind = first; kind <= last; ++kind) {
+        // Inverse transforms due after this slot (two call sites):
+        //   2 <= q < k:  c'_jj alone                      -> ACC_jj
+        //   q == k:      c'_jj (k >= 2) and v together    -> ACC_jj, v in registers
+        //   q == k + 1:  c'_0 and c'_i together           -> ACC_0, ACC_i
+        const bool pair = (q == k && k >= 2) || q == k + 1;
+        const bool single = (q >= 2 && q < k) || (q == k && k == 1);
+        if (pair) {
+            const bool last = (q == k + 1);
+            E y[2][8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                y[0][c] = last ? C0[c] : CJ[c];
+                y[1][c] = last ? CI[c] : V[c];
+            }
+            NT::template inverse<2>(y, tid, twi, xbuf);
+            uint32_t *d0 = acc + (last ? 0 : jj) * N;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) d0[tid + T * c] += F::to_u32(y[0][c]);
+            if (last) {
+                uint32_t *d1 = acc + i * N;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) d1[tid + T * c] += F::to_u32(y[1][c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) vv[c] = F::to_u32(y[1][c]);
+            }
+        } else if (single) {
+            const bool is_v = (q == k);
             E y[1][8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                y[0][c] = kind == 0 ? CJ[c] : (kind == 1 ? V[c] : (kind == 2 ? C0[c] : CI[c]));
+            for (int c = 0; c < 8; ++c) y[0][c] = is_v ? V[c] : CJ[c];
             NT::template inverse<1>(y, tid, twi, xbuf);
-            if (kind == 1) {
+            if (is_v) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) vv[c] = F::to_u32(y[0][c]);
             } else {
-                uint32_t *dst = acc + (kind == 0 ? jj : (kind == 2 ? 0 : i)) * N;
+                uint32_t *dst = acc + jj * N;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) dst[tid + T * c] += F::to_u32(y[0][c]);
             }
