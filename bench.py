@@ -123,6 +123,8 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- roofline bookkeeping
 def work_per_cmux(P, form="ntt"):
     """Algorithmic work of one CMux step, in the unit of the form's ceiling.
+    Tensor form: FLOPs of the dense products -- (2k+4) d Toeplitz products
+    per step, each 4 byte planes x N^2 multiply-accumulates.
     NTT forms: modular multiplies -- (k+2)(d+1) length-N transforms of
     (N/2) log2 N butterflies plus (2k+4) d N pointwise products (hybrid
     product, phase A and B), once per prime.  FFT form: FP64 instructions
@@ -131,6 +133,8 @@ def work_per_cmux(P, form="ntt"):
     M = N/2 folded points."""
     k, d, N = P["k"], P["d"], P["N"]
     logn = N.bit_length() - 1
+    if form == "tc":  # FLOPs (2 per multiply-accumulate) of the dense Toeplitz products, 4 byte planes
+        return 2 * (2 * (k + 1) * d + 2 * d) * 4 * N * N
     if form == "fft":
         M = N // 2
         return (k + 2) * (d + 1) * ((M // 2) * (logn - 1) * 8 + M * 4) + (2 * k + 4) * d * M * 4
@@ -139,8 +143,19 @@ def work_per_cmux(P, form="ntt"):
 
 
 # Work units per measured butterfly of the ceiling microbenchmark.
-UNITS_PER_BUTTERFLY = {"ntt": 1, "ntt2": 1, "fft": 8}
-UNIT_NAME = {"ntt": "G modmul/s", "ntt2": "G modmul/s", "fft": "G FP64 instr/s"}
+UNITS_PER_BUTTERFLY = {"ntt": 1, "ntt2": 1, "fft": 8, "tc": 2}
+UNIT_NAME = {"ntt": "G modmul/s", "ntt2": "G modmul/s", "fft": "G FP64 instr/s", "tc": "TFLOP/s"}
+FORM_DESC = {"ntt": "ntt64 (exact, Goldilocks prime)",
+             "ntt2": "ntt2x30 (exact, two 30-bit primes + CRT)",
+             "fft": "fft64 (FP64, rounded; approximate)",
+             "tc": "tc-bf16 (exact, tensor-core Toeplitz products of key byte planes)"}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
 
 
 def kernel_source_hash():
@@ -212,7 +227,11 @@ def run_ours(args):
 
     # product form, then autotune the blind-rotation variant on a sample of random ciphertexts
     ctx.set_form(args.form)
-    variant, variant_ms = ctx.autotune(min(args.autotune_gates, G))
+    if args.variant >= 0:
+        ctx.set_variant(args.variant)
+        variant, variant_ms = args.variant, None
+    else:
+        variant, variant_ms = ctx.autotune(min(args.autotune_gates, G))
 
     # warm-up (also uploads the keys)
     for _ in range(args.warmup):
@@ -325,40 +344,55 @@ def run_ours(args):
                            for t, a, b in zip(ts, x1.astype(int), x2.astype(int))], np.uint8)
             dt_, d1, d2 = tdev(ts.astype(np.uint8)), tdev(e1), tdev(e2)
             do = torch.zeros((Gs, ck.W), dtype=torch.int32, device="cuda")
-            for form in ("ntt", "ntt2", "fft"):
+            for form in ("ntt", "ntt2", "fft", "tc"):
+                Gf = Gs if form != "tc" else 2048  # the O(N^2) form: one 2048-gate wave
                 ck.set_form(form)
                 ck.autotune(1024)
-                ck.gates(dt_, d1, d2, do)
+                ck.gates(dt_[:Gf], d1[:Gf], d2[:Gf], do[:Gf])
                 torch.cuda.synchronize()
                 s0 = torch.cuda.Event(enable_timing=True)
                 s1 = torch.cuda.Event(enable_timing=True)
                 s0.record(stream)
-                ck.gates(dt_, d1, d2, do)
+                ck.gates(dt_[:Gf], d1[:Gf], d2[:Gf], do[:Gf])
                 s1.record(stream)
                 torch.cuda.synchronize()
                 ms = s0.elapsed_time(s1)
-                sweep.append({"parties": kk, "form": form, "gates": Gs, "gates_per_s": Gs / (ms * 1e-3),
-                              "decrypt_ok": bool(np.array_equal(ck.decrypt(do), tr)),
+                sweep.append({"parties": kk, "form": form, "gates": Gf, "gates_per_s": Gf / (ms * 1e-3),
+                              "decrypt_ok": bool(np.array_equal(ck.decrypt(do[:Gf]), tr[:Gf])),
                               "active_cmux_steps_per_gate": kk * Pk["n"]})
             ck.close()
 
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
     mm_per_gate = work_per_cmux(P, args.form) * P["k"] * P["n"]
-    achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / 1e9
-    peak = (B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / 1e9
-            * UNITS_PER_BUTTERFLY[args.form])
-    traffic_pg = ncu_traffic_per_gate()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT_NAME[args.form],
-                "frac": achieved / peak, "traffic": (traffic_pg * G if traffic_pg is not None else None),
-                "kernel": "bootstrap_ntt_kernel<%s, 10, variant %d>" % (args.form, variant),
-                "algorithmic_work_per_gate": mm_per_gate,
-                "peak_source": ("measured: register-resident butterfly loop of the same arithmetic on every SM "
-                                "(mk_measure_butterfly_rate, %s)"
-                                % {"ntt": "Goldilocks 64-bit, one modmul per butterfly",
-                                   "ntt2": "Harvey/Shoup mod a 30-bit prime, one modmul per butterfly",
-                                   "fft": "complex FP64, 8 FP64 instructions per butterfly"}[args.form]),
-                "br_share_of_step": br_ms / total_ms if total_ms else None}
+    scale = 1e12 if args.form == "tc" else 1e9
+    achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / scale
+    ceiling = (B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / scale
+               * UNITS_PER_BUTTERFLY[args.form])
+    traffic_pg = ncu_traffic_per_gate() if args.form == "ntt2" else None
+    if args.form == "tc":
+        mp = measured_peaks()
+        peak = mp["bf16_tflops_sustained"] if mp else 1700.0
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "blind rotation, tensor form (tc_products_kernel + digit kernels)",
+                    "algorithmic_work_per_gate": mm_per_gate,
+                    "peak_source": ("measured bf16 dense GEMM, sustained (MEASURED_PEAKS.json)" if mp
+                                    else "fallback 1.7 PFLOP/s sustained"),
+                    "mma_sync_ceiling_tflops": ceiling,
+                    "frac_of_mma_sync_ceiling": achieved / ceiling,
+                    "br_share_of_step": br_ms / total_ms if total_ms else None}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": ceiling, "unit": UNIT_NAME[args.form],
+                    "frac": achieved / ceiling, "traffic": (traffic_pg * G if traffic_pg is not None else None),
+                    "kernel": "bootstrap_ntt_kernel<%s, 10, variant %d>" % (args.form, variant),
+                    "algorithmic_work_per_gate": mm_per_gate,
+                    "peak_source": ("measured: register-resident butterfly loop of the same arithmetic on every "
+                                    "SM (mk_measure_butterfly_rate, %s)"
+                                    % {"ntt": "Goldilocks 64-bit, one modmul per butterfly",
+                                       "ntt2": "Harvey/Shoup mod a 30-bit prime, one modmul per butterfly",
+                                       "fft": "complex FP64, 8 FP64 instructions per butterfly"}[args.form]),
+                    "br_share_of_step": br_ms / total_ms if total_ms else None}
 
     ctx.close()
     if rank != 0:
@@ -371,9 +405,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "parties": 2, "gates_per_step": G, "n": P["n"], "N": P["N"],
                    "bg_bit": P["bg_bit"], "d": P["d"], "ks_bit": P["ks_bit"], "t": P["t"],
                    "sigma_lwe": P["sigma_lwe"], "sigma_rlwe": P["sigma_rlwe"],
-                   "form": {"ntt": "ntt64 (exact, Goldilocks prime)",
-                            "ntt2": "ntt2x30 (exact, two 30-bit primes + CRT)",
-                            "fft": "fft64 (FP64, rounded; approximate)"}[args.form],
+                   "form": FORM_DESC[args.form],
                    "variant": variant, "autotune_ms": variant_ms,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "no flush: per-step working set (BK 82 MB NTT domain + KS 110 MB + 37 MB "
@@ -471,7 +503,9 @@ def main():
     ap.add_argument("--k4-gates", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--autotune-gates", type=int, default=2048)
-    ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2", "fft"])
+    ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2", "fft", "tc"])
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="blind-rotation variant to use instead of autotuning (-1: autotune)")
     ap.add_argument("--sweep", action="store_true",
                     help="also time every product form at 2, 4 and 8 parties (8192 joint-key gates each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

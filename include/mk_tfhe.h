@@ -84,9 +84,9 @@ int mk_ctx_destroy(mk_ctx *ctx);
 int mk_ctx_set_stream(mk_ctx *ctx, void *stream);
 int mk_ctx_get_params(const mk_ctx *ctx, mk_params *out);
 
-/* Negacyclic-product form used by the blind rotation.  The two NTT forms are
- * exact (the product sums are recovered as integers and reduced mod 2^32),
- * so they give bit-identical ciphertexts.  The FP64 FFT form rounds each
+/* Negacyclic-product form used by the blind rotation.  The two NTT forms and
+ * the tensor form are exact (the product sums are recovered as integers and
+ * reduced mod 2^32), so they give bit-identical ciphertexts.  The FP64 FFT form rounds each
  * product to the nearest integer; its error per product is small (well
  * below 2^12 torus32 units) but not zero, so its ciphertexts differ from the
  * exact ones in low bits and, rarely, more (a flipped gadget digit), while
@@ -95,8 +95,17 @@ int mk_ctx_get_params(const mk_ctx *ctx, mk_params *out);
 enum {
     MK_FORM_NTT = 0,  /* NTT over the prime 2^64 - 2^32 + 1 */
     MK_FORM_NTT2 = 1, /* NTTs over the primes 0x3fff4001 and 0x3ffee001, CRT */
-    MK_FORM_FFT = 2   /* FP64 FFT of N/2 folded complex points */
+    MK_FORM_FFT = 2,  /* FP64 FFT of N/2 folded complex points */
+    MK_FORM_TC = 3    /* tensor cores: Toeplitz products of key byte planes and
+                         gadget digits, bf16 operands, fp32 sums (exact) */
 };
+/* MK_FORM_TC runs the blind rotation of a batch as a wave: every CMux step is
+ * a few launches over all gates of the batch, with the accumulators and
+ * digits in a device workspace the context allocates with the keys (about
+ * 4 (3 (k+1) N + k n) + 6 (k+2) N bytes per gate, for up to 4096 gates at a
+ * time).  It needs N in {256, 1024}, d = 3 and bg_bit <= 8 (the exactness
+ * bound |digit| * |key byte| * N <= 2^24); mk_ctx_set_form returns
+ * MK_EPARAMS otherwise. */
 int mk_ctx_set_form(mk_ctx *ctx, int form);
 int mk_ctx_get_form(const mk_ctx *ctx, int *form);
 
@@ -109,7 +118,9 @@ int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
  * `sample_gates` random ciphertexts on the context's device, keeps the
  * fastest for the context and stores it in *best (and, if ms_out is not
  * NULL, each variant's milliseconds in ms_out[0..MK_NUM_VARIANTS-1]).  It
- * synchronises the stream.  No paper counterpart: a tuning aid. */
+ * synchronises the stream.  MK_FORM_FFT and MK_FORM_TC have one kernel for
+ * every variant number: there it times nothing, reports 0 ms and keeps the
+ * variant.  No paper counterpart: a tuning aid. */
 #define MK_NUM_VARIANTS 4
 int mk_ctx_set_variant(mk_ctx *ctx, int variant);
 int mk_ctx_get_variant(const mk_ctx *ctx, int *variant);
@@ -326,10 +337,23 @@ int mk_timing_read(mk_ctx *ctx, int kernel, double *ms_total, uint64_t *launches
  * multiply, add and subtract); MK_FORM_NTT2: Harvey butterflies modulo a
  * 30-bit prime (one Shoup multiply, one conditional subtraction, add, sub);
  * MK_FORM_FFT: complex FP64 butterflies (one complex multiply, two complex
- * additions).
+ * additions); MK_FORM_TC: multiply-accumulates per second of independent
+ * warp-level bf16 m16n8k16 MMAs (the instruction of the tensor form).
  * No paper counterpart: a measurement aid for the roofline of the blind
  * rotation. */
 int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters, double *per_s);
+
+/* The product kernel of MK_FORM_TC on its own, for exactness checks:
+ *   out[g] = sum_{c < nchunks} keys[c] * digits[c][g]   in Z[X]/(X^N + 1) mod 2^32
+ * for g < G.  keys: device uint32 [nchunks][N] (torus32 words); digits:
+ * device int8 [nchunks][G][N], each in [-128, 127]; out: device int32
+ * [G][N] (the torus32 words, as int32).  N in {256, 1024}, G a positive
+ * multiple of 64, 1 <= nchunks <= 3; otherwise MK_EINVAL.  The call
+ * allocates a bf16 copy of the digits, runs on `stream` and synchronises it.
+ * No paper counterpart: the negacyclic product of Section 2 (the hybrid
+ * product's inner step) isolated for testing the tensor form. */
+int mk_tc_negacyclic(int device, void *stream, uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys,
+                     const int8_t *digits, int32_t *out);
 
 #ifdef __cplusplus
 }

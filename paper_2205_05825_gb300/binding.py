@@ -18,7 +18,7 @@ ERRORS = {-1: "MK_EINVAL", -2: "MK_ENOMEM", -3: "MK_EPARAMS", -4: "MK_ETIMEOUT",
 GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
 PRESETS = {"toy": 0, "full": 1, "paper": 2}
 NUM_VARIANTS = 4
-FORMS = {"ntt": 0, "ntt2": 1, "fft": 2}
+FORMS = {"ntt": 0, "ntt2": 1, "fft": 2, "tc": 3}
 
 U32P = ctypes.POINTER(ctypes.c_uint32)
 U8P = ctypes.POINTER(ctypes.c_uint8)
@@ -106,6 +106,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "mk_measure_butterfly_rate": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_int, ctypes.c_uint32,
                                                  ctypes.POINTER(ctypes.c_double)]),
+    "mk_tc_negacyclic": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                        VP, VP, VP]),
 }
 
 _lib = None
@@ -408,14 +410,28 @@ def lin_records(types):
 
 
 def measure_butterfly_rate(device=0, stream=None, iters=4096, form="ntt"):
-    """Butterflies per second on every SM: Goldilocks (form "ntt") or Harvey
-    butterflies modulo a 30-bit prime (form "ntt2") -- the ALU ceiling."""
+    """Butterflies per second on every SM: Goldilocks (form "ntt"), Harvey
+    butterflies modulo a 30-bit prime ("ntt2"), complex FP64 butterflies
+    ("fft") -- the pipe ceiling of each form; for "tc", multiply-accumulates
+    per second of bf16 m16n8k16 MMAs."""
     r = ctypes.c_double()
     rc = load().mk_measure_butterfly_rate(device, ctypes.c_void_p(stream or 0), FORMS.get(form, form), iters,
                                           ctypes.byref(r))
     if rc != MK_OK:
         raise MkError("mk_measure_butterfly_rate: %s" % ERRORS.get(rc, rc))
     return r.value
+
+
+def tc_negacyclic(keys, digits, out, device=0, stream=None):
+    """out[g] = sum_c keys[c] * digits[c][g] (negacyclic, mod 2^32) by the
+    tensor-form product kernel.  keys: device uint32/int32 [nchunks][N];
+    digits: device int8 [nchunks][G][N]; out: device int32 [G][N]."""
+    nch, N = int(keys.shape[0]), int(keys.shape[1])
+    G = int(digits.shape[1])
+    rc = load().mk_tc_negacyclic(device, ctypes.c_void_p(stream or 0), N, G, nch, _dptr(keys), _dptr(digits),
+                                 _dptr(out))
+    if rc != MK_OK:
+        raise MkError("mk_tc_negacyclic: %s" % ERRORS.get(rc, rc))
 
 
 OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3}

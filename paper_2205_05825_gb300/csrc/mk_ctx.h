@@ -298,6 +298,8 @@ struct mk_ctx {
     uint64_t *d_bk = nullptr;   // [k][n][3][d][N]
     uint64_t *d_keyA = nullptr; // [(k+1)][d][N]
     uint32_t *d_ks = nullptr;   // [k][N][t][B'-1][n+1]
+    void *d_tcws = nullptr;     // MK_FORM_TC wave workspace for tc_ws_gates gates
+    uint32_t tc_ws_gates = 0;
     uint32_t *d_ext = nullptr;  // scratch [scratch_gates][k*N+1]
     GateDesc *d_desc = nullptr; // scratch [scratch_gates]
     uint32_t scratch_gates = 0;
@@ -319,7 +321,7 @@ struct mk_ctx {
     DeviceKeys dkeys() const {
         // twiddles: [2][N] of 8-byte (NTT) or 16-byte (NTT2) entries; FFT: one [3][N/2] table
         const size_t half = (form == MK_FORM_NTT2 ? 16 : (form == MK_FORM_FFT ? 0 : 8)) * (size_t)P.N;
-        return DeviceKeys{d_tw, (const unsigned char *)d_tw + half, d_bk, d_keyA, d_ks};
+        return DeviceKeys{d_tw, (const unsigned char *)d_tw + half, d_bk, d_keyA, d_ks, d_tcws, tc_ws_gates};
     }
 };
 

@@ -162,6 +162,9 @@ void free_device(mk_ctx *c) {
     cudaFree(c->d_ks);
     cudaFree(c->d_ext);
     cudaFree(c->d_desc);
+    cudaFree(c->d_tcws);
+    c->d_tcws = nullptr;
+    c->tc_ws_gates = 0;
     c->plans.clear();
     c->d_tw = nullptr;
     c->d_bk = c->d_keyA = nullptr;
@@ -231,6 +234,15 @@ int ensure_device_keys(mk_ctx *c) {
         });
         for (size_t r = 0; r < keyA_entries; ++r)
             c->fft.to_device(keyA_src(r), reinterpret_cast<double *>(h_keyA.data() + r * N), r < d);
+    } else if (c->form == MK_FORM_TC) {
+        // torus32 words, 4 bytes per coefficient in the same order; [0] = -a
+        uint32_t *bk32 = reinterpret_cast<uint32_t *>(h_bk.data());
+        uint32_t *kA32 = reinterpret_cast<uint32_t *>(h_keyA.data());
+        parallel_for(bk_entries, [&](size_t e) { std::memcpy(bk32 + e * N, bk_src(e), (size_t)N * 4); });
+        for (size_t r = 0; r < keyA_entries; ++r) {
+            const uint32_t *src = keyA_src(r);
+            for (uint32_t m = 0; m < N; ++m) kA32[r * N + m] = r < d ? 0u - src[m] : src[m];
+        }
     } else {
         if (!c->ntt_p1.N && !(c->ntt_p1.init(kP1, N) && c->ntt_p2.init(kP2, N)))
             return fail(c, MK_EPARAMS, "ring dimension not supported by the two-prime NTT");
@@ -260,11 +272,17 @@ int ensure_device_keys(mk_ctx *c) {
     if (!c->d_bk) MK_CUDA(c, cudaMalloc(&c->d_bk, h_bk.size() * 8));
     if (!c->d_keyA) MK_CUDA(c, cudaMalloc(&c->d_keyA, h_keyA.size() * 8));
     if (!c->d_ks) MK_CUDA(c, cudaMalloc(&c->d_ks, (size_t)k * c->ks_words() * 4));
+    if (c->form == MK_FORM_TC && !c->d_tcws) {
+        const uint32_t gates = kTcWaveGates;
+        MK_CUDA(c, cudaMalloc(&c->d_tcws, tc_workspace_bytes(c->shape(), gates)));
+        c->tc_ws_gates = gates;
+    }
     // Work already enqueued may still read the previous keys.
     MK_CUDA(c, cudaStreamSynchronize(c->stream));
     MK_CUDA(c, cudaMemcpy(c->d_tw, h_tw.data(), h_tw.size(), cudaMemcpyHostToDevice));
-    MK_CUDA(c, cudaMemcpy(c->d_bk, h_bk.data(), h_bk.size() * 8, cudaMemcpyHostToDevice));
-    MK_CUDA(c, cudaMemcpy(c->d_keyA, h_keyA.data(), h_keyA.size() * 8, cudaMemcpyHostToDevice));
+    const size_t coef_bytes = c->form == MK_FORM_TC ? 4 : 8;
+    MK_CUDA(c, cudaMemcpy(c->d_bk, h_bk.data(), h_bk.size() * coef_bytes, cudaMemcpyHostToDevice));
+    MK_CUDA(c, cudaMemcpy(c->d_keyA, h_keyA.data(), h_keyA.size() * coef_bytes, cudaMemcpyHostToDevice));
     for (uint32_t i = 0; i < k; ++i)
         MK_CUDA(c, cudaMemcpy(c->d_ks + (size_t)i * c->ks_words(), c->party[i].ks.data(), c->ks_words() * 4,
                               cudaMemcpyHostToDevice));
@@ -512,8 +530,14 @@ int mk_ctx_get_params(const mk_ctx *c, mk_params *out) {
 
 int mk_ctx_set_form(mk_ctx *c, int form) {
     if (!c) return MK_EINVAL;
-    if (form != MK_FORM_NTT && form != MK_FORM_NTT2 && form != MK_FORM_FFT)
+    if (form != MK_FORM_NTT && form != MK_FORM_NTT2 && form != MK_FORM_FFT && form != MK_FORM_TC)
         return fail(c, MK_EINVAL, "unknown product form");
+    if (form == MK_FORM_TC) {
+        LaunchShape S = c->shape();
+        S.form = form;
+        if (!tc_shape_supported(S))
+            return fail(c, MK_EPARAMS, "the tensor form needs N in {256, 1024}, d = 3 and bg_bit <= 8");
+    }
     if (form != c->form) c->dev_keys_valid = false;  // the NTT-domain keys are rebuilt on next use
     c->form = form;
     return MK_OK;
@@ -548,6 +572,12 @@ int mk_autotune(mk_ctx *c, uint32_t sample_gates, int *best, float *ms_out) {
     if (!c || sample_gates == 0) return MK_EINVAL;
     int rc = device_ready(c, sample_gates);
     if (rc) return rc;
+    if (c->form == MK_FORM_FFT || c->form == MK_FORM_TC) {  // one kernel serves every variant number
+        if (ms_out)
+            for (int v = 0; v < kNumVariants; ++v) ms_out[v] = 0.f;
+        if (best) *best = c->variant;
+        return MK_OK;
+    }
     const size_t W = c->W();
     const uint32_t cnt = std::min<uint32_t>(sample_gates, c->max_batch);
     // Random ciphertexts: every CMux step is active, as for real multi-party inputs.
@@ -1144,7 +1174,8 @@ int mk_timing_read(mk_ctx *c, int kernel, double *ms_total, uint64_t *launches) 
 }
 
 int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters, double *per_s) {
-    if (!per_s || iters == 0 || (form != MK_FORM_NTT && form != MK_FORM_NTT2 && form != MK_FORM_FFT))
+    if (!per_s || iters == 0 ||
+        (form != MK_FORM_NTT && form != MK_FORM_NTT2 && form != MK_FORM_FFT && form != MK_FORM_TC))
         return MK_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return MK_EDEVICE;
     cudaDeviceProp prop;
@@ -1160,6 +1191,7 @@ int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters
     auto launch = [&](uint32_t it) {
         if (form == MK_FORM_NTT) return launch_butterfly_peak(blocks, threads, it, sink, st);
         if (form == MK_FORM_FFT) return launch_butterfly_peak_fft(blocks, threads, it, reinterpret_cast<double *>(sink), st);
+        if (form == MK_FORM_TC) return launch_mma_peak(blocks, threads, it, reinterpret_cast<float *>(sink), st);
         return launch_butterfly_peak2(blocks, threads, it, reinterpret_cast<uint32_t *>(sink), st);
     };
     if (launch(iters / 8 + 1) != cudaSuccess) rc = MK_EDEVICE;  // warm-up
@@ -1169,10 +1201,28 @@ int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters
     if (cudaEventSynchronize(b) != cudaSuccess) rc = MK_EDEVICE;
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
-    *per_s = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+    // MK_FORM_TC: 8 MMAs of 16 x 8 x 16 multiply-accumulates per warp and iteration
+    const double per_thread_iter = form == MK_FORM_TC ? 8.0 * 16 * 8 * 16 / 32 : 8.0;
+    *per_s = (double)blocks * threads * iters * per_thread_iter / (ms * 1e-3);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);
+    return rc;
+}
+
+int mk_tc_negacyclic(int device, void *stream, uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys,
+                     const int8_t *digits, int32_t *out) {
+    if (!keys || !digits || !out || (N != 256 && N != 1024) || G == 0 || G % tc_wave_granularity() || nchunks == 0 ||
+        nchunks > 3)
+        return MK_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return MK_EDEVICE;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *work = nullptr;
+    if (cudaMalloc(&work, (size_t)nchunks * G * N * 2) != cudaSuccess) return MK_ENOMEM;
+    int rc = MK_OK;
+    if (launch_negacyclic_tc(N, G, nchunks, keys, digits, out, work, st) != cudaSuccess) rc = MK_EDEVICE;
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = MK_EDEVICE;
+    cudaFree(work);
     return rc;
 }
 

@@ -39,12 +39,16 @@ struct DeviceKeys {
     const void *bk;       // [k][n][3][d][N] NTT domain, bit-reversed order, times N^-1
     const void *keyA;     // [(k+1)][d][N]: [0] = NTT(-a), [j] = NTT(pk_j), times N^-1
     const uint32_t *ks;   // [k][N][t][B'-1][n+1] torus32
+    // MK_FORM_TC: bk and keyA hold torus32 words in the same order ([0] = -a);
+    // the wave workspace holds tc_ws_gates gates (a multiple of 64).
+    void *tc_ws;
+    uint32_t tc_ws_gates;
 };
 
 struct LaunchShape {
     uint32_t n, N, logN, k, d, bg_bit, ks_bit, t;
     int variant;  // blind-rotation variant (see kVariantNpf)
-    int form;     // MK_FORM_NTT or MK_FORM_NTT2
+    int form;     // MK_FORM_*
 };
 
 // a1-a8: linear part, window shift, modulus switch, blind rotation (NTT form),
@@ -92,6 +96,23 @@ MK_DECLARE_BOOTSTRAP_F(10, 0)
 MK_DECLARE_BOOTSTRAP_F(10, 1)
 MK_DECLARE_BOOTSTRAP(8, 2, 0)
 MK_DECLARE_BOOTSTRAP(10, 2, 0)
+
+// MK_FORM_TC (mk_tensor.cu): the blind rotation of a batch as a wave of
+// tensor-core Toeplitz products.  Same arguments as the launchers above;
+// count is processed in waves of K.tc_ws_gates gates.
+cudaError_t launch_bootstrap_tc(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc, const uint32_t *ct_a,
+                                const uint32_t *ct_b, const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,
+                                uint32_t *acc_out, uint32_t count, cudaStream_t st);
+bool tc_shape_supported(const LaunchShape &S);
+constexpr uint32_t kTcWaveGates = 4096;  // gates per wave of the context's workspace
+size_t tc_workspace_bytes(const LaunchShape &S, uint32_t gates);
+uint32_t tc_wave_granularity();
+// out[g] = sum_c keys[c] * digits[c][g] (negacyclic, mod 2^32); work holds
+// nchunks * G * N bf16.
+cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys, const int8_t *digits,
+                                 int32_t *out, void *work, cudaStream_t st);
+// Register-resident bf16 m16n8k16 MMA loop: 8 MMAs per warp and iteration.
+cudaError_t launch_mma_peak(uint32_t blocks, uint32_t threads, uint32_t iters, float *sink, cudaStream_t st);
 
 // a9: per-party key switch of ext [count][k*N+1] into out rows desc[g].out
 // (or row g when desc == nullptr).

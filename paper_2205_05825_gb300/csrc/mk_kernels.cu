@@ -293,6 +293,7 @@ cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, cons
                                  const uint32_t *ct_a, const uint32_t *ct_b, uint32_t *ext, uint32_t count,
                                  cudaStream_t st) {
     if (count == 0) return cudaSuccess;
+    if (S.form == MK_FORM_TC) return launch_bootstrap_tc(S, K, desc, ct_a, ct_b, nullptr, -1, ext, nullptr, count, st);
     BootstrapFn f = pick(S);
     if (!f) return cudaErrorInvalidValue;
     return f(S, K, desc, ct_a, ct_b, nullptr, -1, ext, nullptr, count, st);
@@ -301,6 +302,7 @@ cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, cons
 cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, const uint32_t *abar,
                                     uint32_t count, int64_t max_steps, uint32_t *acc, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
+    if (S.form == MK_FORM_TC) return launch_bootstrap_tc(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);
     BootstrapFn f = pick(S);
     if (!f) return cudaErrorInvalidValue;
     return f(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);

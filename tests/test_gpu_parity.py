@@ -186,13 +186,13 @@ def test_full_k2_sampled_bit_exact_and_all_decrypt(full2):
     assert np.array_equal(got[idx], ref)
 
 
-FORM_VARIANTS = [(f, v) for f in ("ntt", "ntt2") for v in range(4)]
+FORM_VARIANTS = [(f, v) for f in ("ntt", "ntt2") for v in range(4)] + [("tc", 0)]
 
 
 @pytest.mark.parametrize("form,variant", FORM_VARIANTS)
 def test_toy_every_variant_bit_exact(toy, form, variant):
-    """Each product form (Goldilocks NTT, two-prime NTT) and each kernel
-    variant gives the oracle's ciphertexts."""
+    """Each exact product form (Goldilocks NTT, two-prime NTT, tensor cores)
+    and each kernel variant gives the oracle's ciphertexts."""
     import torch
     from oracle import oracle as o
     P, keys, ctx, g, b1, b2, c1, c2 = toy

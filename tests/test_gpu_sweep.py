@@ -33,7 +33,7 @@ def test_sweep_forms_against_oracle(gpu_ready, k):
     exp = np.array([TRUTH[int(t)](int(x), int(y)) for t, x, y in zip(types, b1, b2)], np.uint8)
     idx = np.arange(SAMPLED[k])
     ref = o.gates(P, keys, types[idx], c1[idx], c2[idx])
-    for form in ("ntt", "ntt2", "fft"):
+    for form in ("ntt", "ntt2", "fft", "tc"):
         ctx.set_form(form)
         out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
         ctx.gates(to_dev(types.astype(np.uint8)), to_dev(c1), to_dev(c2), out)
