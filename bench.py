@@ -226,6 +226,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     # product form, then autotune the blind-rotation variant on a sample of random ciphertexts
+    form_ms = None
+    if args.form == "auto":  # the product-form autotuner over the exact forms
+        args.form, form_ms = ctx.autotune_form(min(args.autotune_gates, G), forms=("ntt", "ntt2", "tc"))
     ctx.set_form(args.form)
     if args.variant >= 0:
         ctx.set_variant(args.variant)
@@ -406,7 +409,7 @@ def run_ours(args):
                    "bg_bit": P["bg_bit"], "d": P["d"], "ks_bit": P["ks_bit"], "t": P["t"],
                    "sigma_lwe": P["sigma_lwe"], "sigma_rlwe": P["sigma_rlwe"],
                    "form": FORM_DESC[args.form],
-                   "variant": variant, "autotune_ms": variant_ms,
+                   "variant": variant, "autotune_ms": variant_ms, "form_autotune_ms": form_ms,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "no flush: per-step working set (BK 82 MB NTT domain + KS 110 MB + 37 MB "
                          "ciphertexts) exceeds the 129 MB L2"},
@@ -503,7 +506,8 @@ def main():
     ap.add_argument("--k4-gates", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--autotune-gates", type=int, default=2048)
-    ap.add_argument("--form", default="ntt2", choices=["ntt", "ntt2", "fft", "tc"])
+    ap.add_argument("--form", default="auto", choices=["auto", "ntt", "ntt2", "fft", "tc"],
+                    help="product form; auto = the library's form autotuner over the exact forms")
     ap.add_argument("--variant", type=int, default=-1,
                     help="blind-rotation variant to use instead of autotuning (-1: autotune)")
     ap.add_argument("--sweep", action="store_true",

@@ -126,6 +126,18 @@ int mk_ctx_set_variant(mk_ctx *ctx, int variant);
 int mk_ctx_get_variant(const mk_ctx *ctx, int *variant);
 int mk_autotune(mk_ctx *ctx, uint32_t sample_gates, int *best, float *ms_out);
 
+/* Product-form autotuner.  forms: a set of bits (1 << MK_FORM_*).  For each
+ * form in the set that the parameters support, the call builds that form's
+ * device keys, autotunes its variants (mk_autotune) and times one launch of
+ * min(sample_gates, batch) random ciphertexts; it keeps the fastest form and
+ * variant for the context and stores the form in *best_form (if not NULL)
+ * and each tried form's milliseconds in ms_out[MK_FORM_*] (0 for the rest;
+ * ms_out may be NULL).  Leave MK_FORM_FFT out of the set to choose among the
+ * exact forms only.  It synchronises the stream.  MK_EPARAMS if no form in
+ * the set supports the parameters.  No paper counterpart: a tuning aid. */
+#define MK_NUM_FORMS 4
+int mk_autotune_form(mk_ctx *ctx, uint32_t sample_gates, uint32_t forms, int *best_form, float *ms_out);
+
 /* Message of the last failed call on ctx (never NULL). */
 const char *mk_last_error(const mk_ctx *ctx);
 

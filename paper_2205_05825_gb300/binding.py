@@ -85,6 +85,8 @@ _SIGS = {
     "mk_ctx_get_variant": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
     "mk_autotune": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]),
+    "mk_autotune_form": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "mk_add_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
     "mk_sub_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
     "mk_mul_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
@@ -229,6 +231,18 @@ class Context:
         ms = (ctypes.c_float * NUM_VARIANTS)()
         self._check(self.L.mk_autotune(self.h, sample_gates, ctypes.byref(best), ms), "mk_autotune")
         return best.value, list(ms)
+
+    def autotune_form(self, sample_gates, forms=("ntt", "ntt2", "tc")):
+        """Time each product form (with its best variant); keep the fastest.
+        -> (best form name, {form name: ms})."""
+        mask = 0
+        for f in forms:
+            mask |= 1 << FORMS[f]
+        best = ctypes.c_int()
+        ms = (ctypes.c_float * len(FORMS))()
+        self._check(self.L.mk_autotune_form(self.h, sample_gates, mask, ctypes.byref(best), ms), "mk_autotune_form")
+        names = {v: k for k, v in FORMS.items()}
+        return names[best.value], {names[i]: ms[i] for i in range(len(FORMS)) if ms[i] > 0}
 
     def sync(self):
         self._check(self.L.mk_sync(self.h), "mk_sync")

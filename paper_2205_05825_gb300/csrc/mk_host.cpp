@@ -431,6 +431,47 @@ int run_circuit(mk_ctx *c, int op, uint32_t k, const uint32_t *d_a, const uint32
     return MK_OK;
 }
 
+// Random ciphertexts (every CMux step active, as for real multi-party
+// inputs): two operand blocks of cnt rows each, for the tuners.
+int sample_inputs(mk_ctx *c, uint32_t cnt, uint32_t **d_in) {
+    const size_t W = c->W();
+    std::vector<uint32_t> h((size_t)2 * cnt * W);
+    const Philox r(0xA5A5A5A5ull, 0x7F);
+    for (size_t q = 0; q < h.size(); ++q) h[q] = r.word(q);
+    MK_CUDA(c, cudaMalloc(d_in, h.size() * 4));
+    const cudaError_t e = cudaMemcpy(*d_in, h.data(), h.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(*d_in);
+        *d_in = nullptr;
+        return cuda_fail(c, e, "tuner inputs");
+    }
+    return MK_OK;
+}
+
+// One untimed and one timed bootstrap launch of cnt NAND gates on the
+// context's current form and variant (needs device_ready(c, cnt)).
+cudaError_t time_sample(mk_ctx *c, uint32_t cnt, const uint32_t *d_in, float *ms) {
+    const size_t W = c->W();
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaError_t err = launch_desc_uniform(MK_NAND, c->d_desc, 0, cnt, c->stream);
+    if (err == cudaSuccess)
+        err = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_in, d_in + (size_t)cnt * W, c->d_ext, cnt,
+                                   c->stream);
+    cudaEventRecord(a, c->stream);
+    if (err == cudaSuccess)
+        err = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_in, d_in + (size_t)cnt * W, c->d_ext, cnt,
+                                   c->stream);
+    cudaEventRecord(b, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(b);
+    *ms = 0;
+    if (err == cudaSuccess) cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return err;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -578,39 +619,18 @@ int mk_autotune(mk_ctx *c, uint32_t sample_gates, int *best, float *ms_out) {
         if (best) *best = c->variant;
         return MK_OK;
     }
-    const size_t W = c->W();
     const uint32_t cnt = std::min<uint32_t>(sample_gates, c->max_batch);
-    // Random ciphertexts: every CMux step is active, as for real multi-party inputs.
-    std::vector<uint32_t> h((size_t)2 * cnt * W);
-    const Philox r(0xA5A5A5A5ull, 0x7F);
-    for (size_t q = 0; q < h.size(); ++q) h[q] = r.word(q);
-    uint32_t *d_in = nullptr, *d_out = nullptr;
-    MK_CUDA(c, cudaMalloc(&d_in, h.size() * 4));
-    if (cudaMalloc(&d_out, (size_t)cnt * W * 4) != cudaSuccess) {
-        cudaFree(d_in);
-        return fail(c, MK_ENOMEM, "autotune scratch");
-    }
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    uint32_t *d_in = nullptr;
+    rc = sample_inputs(c, cnt, &d_in);
+    if (rc) return rc;
     int bestv = c->variant;
     float bestms = 1e30f;
-    cudaError_t err = cudaMemcpyAsync(d_in, h.data(), h.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t err = cudaSuccess;
     const int saved = c->variant;
     for (int v = 0; v < kNumVariants && err == cudaSuccess; ++v) {
         c->variant = v;
-        err = launch_desc_uniform(MK_NAND, c->d_desc, 0, cnt, c->stream);
-        if (err == cudaSuccess)
-            err = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_in, d_in + (size_t)cnt * W, c->d_ext, cnt,
-                                       c->stream);
-        cudaEventRecord(a, c->stream);
-        if (err == cudaSuccess)
-            err = launch_bootstrap_ntt(c->shape(), c->dkeys(), c->d_desc, d_in, d_in + (size_t)cnt * W, c->d_ext, cnt,
-                                       c->stream);
-        cudaEventRecord(b, c->stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(b);
         float ms = 0;
-        if (err == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+        err = time_sample(c, cnt, d_in, &ms);
         if (ms_out) ms_out[v] = ms;
         if (err == cudaSuccess && ms < bestms) {
             bestms = ms;
@@ -618,12 +638,55 @@ int mk_autotune(mk_ctx *c, uint32_t sample_gates, int *best, float *ms_out) {
         }
     }
     c->variant = (err == cudaSuccess) ? bestv : saved;
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     cudaFree(d_in);
-    cudaFree(d_out);
     if (err != cudaSuccess) return cuda_fail(c, err, "autotune");
     if (best) *best = c->variant;
+    return MK_OK;
+}
+
+int mk_autotune_form(mk_ctx *c, uint32_t sample_gates, uint32_t forms, int *best_form, float *ms_out) {
+    if (!c) return MK_EINVAL;
+    if (sample_gates == 0 || forms == 0 || (forms >> MK_NUM_FORMS))
+        return fail(c, MK_EINVAL, "sample_gates must be positive and forms a non-empty set of MK_FORM_* bits");
+    if (ms_out)
+        for (int f = 0; f < MK_NUM_FORMS; ++f) ms_out[f] = 0.f;
+    const int saved_form = c->form, saved_variant = c->variant;
+    int bestf = -1, bestv = saved_variant;
+    float bestms = 1e30f;
+    for (int f = 0; f < MK_NUM_FORMS; ++f) {
+        if (!((forms >> f) & 1u)) continue;
+        if (mk_ctx_set_form(c, f) != MK_OK) continue;  // not supported by these parameters
+        int v = c->variant;
+        int rc = mk_autotune(c, sample_gates, &v, nullptr);
+        uint32_t *d_in = nullptr;
+        const uint32_t cnt = std::min<uint32_t>(sample_gates, c->max_batch);
+        if (rc == MK_OK) rc = sample_inputs(c, cnt, &d_in);
+        float ms = 0;
+        if (rc == MK_OK) {
+            const cudaError_t err = time_sample(c, cnt, d_in, &ms);
+            cudaFree(d_in);
+            if (err != cudaSuccess) rc = cuda_fail(c, err, "form autotune");
+        }
+        if (rc != MK_OK) {
+            mk_ctx_set_form(c, saved_form);
+            c->variant = saved_variant;
+            return rc;
+        }
+        if (ms_out) ms_out[f] = ms;
+        if (ms < bestms) {
+            bestms = ms;
+            bestf = f;
+            bestv = v;
+        }
+    }
+    if (bestf < 0) {
+        mk_ctx_set_form(c, saved_form);
+        c->variant = saved_variant;
+        return fail(c, MK_EPARAMS, "none of the requested product forms supports these parameters");
+    }
+    mk_ctx_set_form(c, bestf);
+    c->variant = bestv;
+    if (best_form) *best_form = bestf;
     return MK_OK;
 }
 

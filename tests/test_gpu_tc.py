@@ -154,3 +154,29 @@ def test_tc_rejects_unsupported_params(gpu_ready):
     with pytest.raises(B.MkError):
         ctx.set_form("tc")
     ctx.close()
+
+
+def test_autotune_form_keeps_the_fastest_exact_form(gpu_ready):
+    """mk_autotune_form over the exact forms: every form is timed, the context
+    keeps the fastest, and its gates still equal the oracle's."""
+    import torch
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.toy_params(2)
+    keys = oracle_keys(P)
+    ctx = B.Context(P, W.CRS_SEED, device=0)
+    ctx.import_oracle_keys(keys)
+    best, ms = ctx.autotune_form(256, forms=("ntt", "ntt2", "tc"))
+    assert set(ms) == {"ntt", "ntt2", "tc"}
+    assert best == min(ms, key=ms.get)
+    assert ctx.get_form() == B.FORMS[best]
+    g, b1, b2 = W.truth_table_inputs()
+    c1 = o.encrypt(P, keys, 0, b1, W.encryption_seed(1, 0))
+    c2 = o.encrypt(P, keys, 1, b2, W.encryption_seed(1, 1))
+    out = torch.zeros((len(g), ctx.W), dtype=torch.int32, device="cuda")
+    ctx.gates(to_dev(g.astype(np.uint8)), to_dev(c1), to_dev(c2), out)
+    assert np.array_equal(from_dev(out), o.gates(P, keys, g, c1, c2))
+    with pytest.raises(B.MkError):
+        ctx.autotune_form(256, forms=())
+    ctx.close()
