@@ -115,7 +115,9 @@ cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const
 cudaError_t launch_mma_peak(uint32_t blocks, uint32_t threads, uint32_t iters, float *sink, cudaStream_t st);
 
 // a9: per-party key switch of ext [count][k*N+1] into out rows desc[g].out
-// (or row g when desc == nullptr).
+// (or row g when desc == nullptr).  From kKeyswitchBatchMin gates on (and for
+// 2-bit digits) a CTA serves a group of gates from each key row it reads.
+constexpr uint32_t kKeyswitchBatchMin = 64;
 cudaError_t launch_keyswitch(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                              const uint32_t *ext, uint32_t *out, uint32_t count, cudaStream_t st);
 

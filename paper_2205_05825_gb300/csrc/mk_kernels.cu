@@ -60,6 +60,94 @@ __global__ void keyswitch_kernel(LaunchShape S, const uint32_t *__restrict__ ks,
     }
 }
 
+// Batched key switch for 2-bit digits (three rows per digit level): a CTA
+// owns KS_GB gates and KS_CX output columns, so every key-switch row it reads
+// from L2 serves all its gates.  Per party i and block of KS_JB coefficients
+// the gates' digit words (a_{i,j} rounded to ks_bit*t bits) are staged in
+// shared memory; per (j, l) each thread puts its column of the rows
+// KS_i[j][l][0..2] into private shared-memory slots 1..3 (slot 0 holds zero)
+// and every gate adds the slot its digit delta_l selects.  The row loads of
+// the next (j, l) are issued before the adds of the current one.
+constexpr int KS_GB = 32, KS_CX = 128, KS_JB = 64;
+
+__global__ void __launch_bounds__(KS_CX) keyswitch_batched_kernel(LaunchShape S, const uint32_t *__restrict__ ks,
+                                                                  const GateDesc *__restrict__ desc,
+                                                                  const uint32_t *__restrict__ ext,
+                                                                  uint32_t *__restrict__ out, uint32_t count) {
+    __shared__ __align__(16) uint32_t s_dw[KS_JB * KS_GB];
+    __shared__ uint32_t s_rows[4 * KS_CX];
+    const uint32_t n = S.n, N = S.N, k = S.k, t = S.t;
+    const uint32_t E = k * N + 1, W = k * n + 1;
+    const uint32_t dbits = 2 * t;
+    const uint32_t round_off = 1u << (32 - dbits - 1);
+    const uint32_t g0 = blockIdx.x * KS_GB;
+    const uint32_t ng = min((uint32_t)KS_GB, count - g0);
+    const uint32_t tx = threadIdx.x;
+    const uint32_t x = blockIdx.y * KS_CX + tx;  // output column
+    const uint32_t xc = x <= n ? x : n;          // columns past n read column n and write nothing
+    const size_t rowlen = n + 1;
+    const size_t jstride = (size_t)t * 3 * rowlen;  // rows of one coefficient
+    s_rows[tx] = 0;  // slot 0: digit 0 adds nothing
+    uint32_t acc[KS_GB];
+#pragma unroll
+    for (int g = 0; g < KS_GB; ++g) acc[g] = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+        const uint32_t *ksi = ks + (size_t)i * N * jstride + xc;
+        for (uint32_t j0 = 0; j0 < N; j0 += KS_JB) {
+            __syncthreads();  // the previous block's digit words are consumed
+            for (uint32_t q = tx; q < KS_JB * KS_GB; q += KS_CX) {
+                const uint32_t g = q / KS_JB, jj = q % KS_JB;
+                uint32_t w = 0;
+                if (g < ng) w = (ext[(size_t)(g0 + g) * E + i * N + j0 + jj] + round_off) >> (32 - dbits);
+                s_dw[jj * KS_GB + g] = w;
+            }
+            __syncthreads();
+            const uint32_t *rows = ksi + (size_t)j0 * jstride;  // (j0, l = 0), advancing by rowlen * 3 per l
+            uint32_t r0 = __ldg(rows), r1 = __ldg(rows + rowlen), r2 = __ldg(rows + 2 * rowlen);
+            for (uint32_t jj = 0; jj < KS_JB; ++jj) {
+                uint32_t dw[KS_GB];
+                const uint4 *pw = reinterpret_cast<const uint4 *>(s_dw + jj * KS_GB);
+#pragma unroll
+                for (int q = 0; q < KS_GB / 4; ++q) {
+                    const uint4 v = pw[q];
+                    dw[4 * q] = v.x, dw[4 * q + 1] = v.y, dw[4 * q + 2] = v.z, dw[4 * q + 3] = v.w;
+                }
+                for (uint32_t l = 0; l < t; ++l) {
+                    s_rows[KS_CX + tx] = r0;
+                    s_rows[2 * KS_CX + tx] = r1;
+                    s_rows[3 * KS_CX + tx] = r2;
+                    rows += 3 * rowlen;  // next (j, l); one row past the block's end is never read
+                    if (jj + 1 < KS_JB || l + 1 < t) {
+                        r0 = __ldg(rows), r1 = __ldg(rows + rowlen), r2 = __ldg(rows + 2 * rowlen);
+                    }
+                    const uint32_t sh = dbits - 2 * (l + 1);
+#pragma unroll
+                    for (int g = 0; g < KS_GB; ++g) acc[g] += s_rows[((dw[g] >> sh) & 3u) * KS_CX + tx];
+                }
+            }
+        }
+        if (x < n) {
+#pragma unroll
+            for (int g = 0; g < KS_GB; ++g) {
+                if ((uint32_t)g < ng) {
+                    const uint32_t orow = desc ? desc[g0 + g].out : g0 + g;
+                    out[(size_t)orow * W + i * n + x] = acc[g];
+                }
+                acc[g] = 0;
+            }
+        }
+    }
+    if (x == n) {  // the b column sums over every party
+#pragma unroll
+        for (int g = 0; g < KS_GB; ++g) {
+            if ((uint32_t)g < ng) {
+                const uint32_t orow = desc ? desc[g0 + g].out : g0 + g;
+                out[(size_t)orow * W + k * n] = ext[(size_t)(g0 + g) * E + k * N] + acc[g];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ NOT and descriptors
 __global__ void not_kernel(uint32_t W, const uint32_t *__restrict__ in, uint32_t *__restrict__ out, size_t total) {
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
@@ -318,6 +406,11 @@ cudaError_t launch_modswitch(const LaunchShape &S, const GateDesc *desc, const u
 cudaError_t launch_keyswitch(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                              const uint32_t *ext, uint32_t *out, uint32_t count, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
+    if (S.ks_bit == 2 && count >= kKeyswitchBatchMin) {
+        const dim3 grid((count + KS_GB - 1) / KS_GB, (S.n + 1 + KS_CX - 1) / KS_CX);
+        keyswitch_batched_kernel<<<grid, KS_CX, 0, st>>>(S, K.ks, desc, ext, out, count);
+        return cudaGetLastError();
+    }
     const uint32_t threads = ((S.n + 1 + 31) / 32) * 32 > 1024 ? 1024 : ((S.n + 1 + 31) / 32) * 32;
     const size_t sm = sizeof(uint32_t) * (S.k * S.N + 1);
     cudaError_t e = cudaFuncSetAttribute(keyswitch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -261,3 +261,17 @@ def test_full_k4_sampled_bit_exact(gpu_ready):
     idx = np.array([0, 63])
     assert np.array_equal(got[idx], o.gates(P, keys, types[idx], c1[idx], c2[idx]))
     ctx.close()
+
+
+@pytest.mark.parametrize("count", [63, 64, 65, 100])
+def test_toy_keyswitch_batch_boundaries(toy, count):
+    """Key switch through the per-gate kernel (< 64 gates) and the batched
+    kernel (>= 64: groups of 32 gates, a ragged last group), word for word."""
+    import torch
+    from oracle import oracle as o
+    P, keys, ctx = toy[:3]
+    rng = np.random.default_rng(count)
+    ext = rng.integers(0, 2 ** 32, size=(count, ctx.E), dtype=np.uint64).astype(np.uint32)
+    out = torch.zeros((count, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.stage_keyswitch(to_dev(ext), out)
+    assert np.array_equal(from_dev(out), o.keyswitch(P, keys, ext))
