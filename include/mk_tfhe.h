@@ -113,6 +113,15 @@ int mk_ctx_get_form(const mk_ctx *ctx, int *form);
  * scratch space grows with it).  1 gives the one-gate-per-launch form. */
 int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
 
+/* The k-bit operators evaluate their netlist level by level.  With graphs on
+ * (the default) the level loop of each (operator, width, pairs) plan is
+ * captured once as a CUDA graph on a stream the context owns and replayed on
+ * the context's stream; it is captured again when the form, the variant or
+ * the key buffers change.  Graphs are not used while timing is enabled
+ * (mk_timing_enable) or with MK_FORM_TC.  No paper counterpart: launch
+ * overhead only, results are identical either way. */
+int mk_ctx_set_graphs(mk_ctx *ctx, int on);
+
 /* Blind-rotation kernel variants (same results, different register/occupancy
  * trade-offs): 0..MK_NUM_VARIANTS-1.  mk_autotune times every variant on
  * `sample_gates` random ciphertexts on the context's device, keeps the

@@ -85,6 +85,7 @@ _SIGS = {
     "mk_ctx_get_variant": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
     "mk_autotune": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]),
+    "mk_ctx_set_graphs": (ctypes.c_int, [VP, ctypes.c_int]),
     "mk_autotune_form": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
     "mk_add_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
@@ -231,6 +232,10 @@ class Context:
         ms = (ctypes.c_float * NUM_VARIANTS)()
         self._check(self.L.mk_autotune(self.h, sample_gates, ctypes.byref(best), ms), "mk_autotune")
         return best.value, list(ms)
+
+    def set_graphs(self, on):
+        """Replay each operator's level loop as a captured CUDA graph (default on)."""
+        self._check(self.L.mk_ctx_set_graphs(self.h, 1 if on else 0), "mk_ctx_set_graphs")
 
     def autotune_form(self, sample_gates, forms=("ntt", "ntt2", "tc")):
         """Time each product form (with its best variant); keep the fastest.

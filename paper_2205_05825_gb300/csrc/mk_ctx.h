@@ -270,7 +270,12 @@ struct CircuitPlan {
     uint32_t *d_pool = nullptr;
     uint32_t *d_ext = nullptr;
     int32_t *d_outs = nullptr;
+    // The level loop captured as a CUDA graph, and what it was captured with.
+    cudaGraphExec_t graph = nullptr;
+    int graph_form = -1, graph_variant = -1;
+    DeviceKeys graph_keys{};
     ~CircuitPlan() {
+        if (graph) cudaGraphExecDestroy(graph);
         cudaFree(d_desc);
         cudaFree(d_pool);
         cudaFree(d_ext);
@@ -306,6 +311,8 @@ struct mk_ctx {
     std::string err;
     // measurement: event pairs around launches, per kernel class
     bool timing = false;
+    bool use_graphs = true;               // circuits replay their level loop as a CUDA graph
+    cudaStream_t capture_stream = nullptr;  // non-default stream the graphs are captured on
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
     std::vector<cudaEvent_t> ev_pool;
     std::map<std::tuple<int, uint32_t, uint32_t>, std::unique_ptr<CircuitPlan>> plans;

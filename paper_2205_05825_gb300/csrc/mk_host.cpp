@@ -164,8 +164,10 @@ void free_device(mk_ctx *c) {
     cudaFree(c->d_desc);
     cudaFree(c->d_tcws);
     c->d_tcws = nullptr;
+    c->plans.clear();  // graphs and plan buffers go before the capture stream
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    c->capture_stream = nullptr;
     c->tc_ws_gates = 0;
-    c->plans.clear();
     c->d_tw = nullptr;
     c->d_bk = c->d_keyA = nullptr;
     c->d_ks = c->d_ext = nullptr;
@@ -391,6 +393,35 @@ int get_plan(mk_ctx *c, int op, uint32_t k, uint32_t pairs, CircuitPlan **out) {
     return MK_OK;
 }
 
+// Capture the level loop of a plan on the context's capture stream.  On any
+// failure the plan keeps no graph and the caller launches directly.
+void capture_levels(mk_ctx *c, CircuitPlan *pl, const LaunchShape &S, const DeviceKeys &K) {
+    if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->capture_stream = nullptr;
+        return;
+    }
+    cudaStream_t cs = c->capture_stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) return;
+    cudaError_t e = cudaSuccess;
+    for (size_t l = 0; e == cudaSuccess && l + 1 < pl->level_off.size(); ++l) {
+        const uint32_t off = pl->level_off[l], cnt = pl->level_off[l + 1] - off;
+        e = launch_bootstrap_ntt(S, K, pl->d_desc + off, pl->d_pool, pl->d_pool, pl->d_ext, cnt, cs);
+        if (e == cudaSuccess) e = launch_keyswitch(S, K, pl->d_desc + off, pl->d_ext, pl->d_pool, cnt, cs);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess && ee == cudaSuccess && g) {
+        if (cudaGraphInstantiate(&pl->graph, g, 0) != cudaSuccess) pl->graph = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // a failed capture leaves no sticky error: the caller launches directly
+    if (pl->graph) {
+        pl->graph_form = c->form;
+        pl->graph_variant = c->variant;
+        pl->graph_keys = K;
+    }
+}
+
 // Evaluate operator `op` on `pairs` operand pairs; outputs [pairs][n_outputs],
 // or, with d_out2, the first half of the outputs into d_out and the second
 // half into d_out2 (quotient and remainder).
@@ -411,7 +442,24 @@ int run_circuit(mk_ctx *c, int op, uint32_t k, const uint32_t *d_a, const uint32
     cudaError_t e = launch_circuit_consts(pl->d_pool, P, W, c->stream);
     if (e == cudaSuccess) e = launch_circuit_inputs(pl->d_pool, d_a, k, P, 2, W, c->stream);
     if (e == cudaSuccess) e = launch_circuit_inputs(pl->d_pool, d_b, k, P, 2 + k, W, c->stream);
-    for (size_t l = 0; e == cudaSuccess && l + 1 < pl->level_off.size(); ++l) {
+    // The level loop reads and writes only the plan's own buffers, so it is
+    // captured once as a CUDA graph (per form, variant and key buffers) and
+    // replayed; the tensor form (thousands of launches per level) and timed
+    // runs launch directly.
+    bool replayed = false;
+    if (e == cudaSuccess && c->use_graphs && !c->timing && c->form != MK_FORM_TC) {
+        if (pl->graph && (pl->graph_form != c->form || pl->graph_variant != c->variant ||
+                          std::memcmp(&pl->graph_keys, &K, sizeof(K)) != 0)) {
+            cudaGraphExecDestroy(pl->graph);
+            pl->graph = nullptr;
+        }
+        if (!pl->graph) capture_levels(c, pl, S, K);
+        if (pl->graph) {
+            e = cudaGraphLaunch(pl->graph, c->stream);
+            replayed = true;
+        }
+    }
+    for (size_t l = 0; !replayed && e == cudaSuccess && l + 1 < pl->level_off.size(); ++l) {
         const uint32_t off = pl->level_off[l], cnt = pl->level_off[l + 1] - off;
         e = timed(c, MK_KERNEL_BOOTSTRAP, [&] {
             return launch_bootstrap_ntt(S, K, pl->d_desc + off, pl->d_pool, pl->d_pool, pl->d_ext, cnt, c->stream);
@@ -587,6 +635,12 @@ int mk_ctx_set_form(mk_ctx *c, int form) {
 int mk_ctx_get_form(const mk_ctx *c, int *form) {
     if (!c || !form) return MK_EINVAL;
     *form = c->form;
+    return MK_OK;
+}
+
+int mk_ctx_set_graphs(mk_ctx *c, int on) {
+    if (!c) return MK_EINVAL;
+    c->use_graphs = on != 0;
     return MK_OK;
 }
 

@@ -115,3 +115,30 @@ def test_full_k4_8bit_add_and_mul(gpu_ready):
     for op in ("add", "mul"):
         _check(P, keys, op, 8, a, b, _run(ctx, op, 8, ca, cb))
     ctx.close()
+
+
+@pytest.mark.parametrize("op", ["add", "mul"])
+def test_toy_graph_replay_matches_direct_launches(toy, op):
+    """The level loop replayed as a captured CUDA graph (twice, so the second
+    call replays the cached graph), launched directly, and launched under
+    timing (which bypasses graphs) give the same ciphertexts; a form change
+    re-captures."""
+    P, keys, ctx = toy
+    a = np.array([-8, 5, -1, 7, 0], np.int64)
+    b = np.array([3, -7, 2, -8, 1], np.int64)
+    ca, cb = _encrypt_operands(P, keys, a, b, 4, 720)
+    ctx.set_graphs(True)
+    g1 = _run(ctx, op, 4, ca, cb)
+    g2 = _run(ctx, op, 4, ca, cb)
+    ctx.set_graphs(False)
+    direct = _run(ctx, op, 4, ca, cb)
+    ctx.set_graphs(True)
+    ctx.timing_enable(True)
+    timed_ = _run(ctx, op, 4, ca, cb)
+    ctx.timing_enable(False)
+    ctx.set_form("ntt")
+    other_form = _run(ctx, op, 4, ca, cb)
+    ctx.set_form("ntt2")
+    assert np.array_equal(g1, direct) and np.array_equal(g2, direct) and np.array_equal(timed_, direct)
+    assert np.array_equal(other_form, direct)
+    _check(P, keys, op, 4, a, b, g1)
