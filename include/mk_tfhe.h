@@ -113,6 +113,18 @@ int mk_ctx_get_form(const mk_ctx *ctx, int *form);
  * scratch space grows with it).  1 gives the one-gate-per-launch form. */
 int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
 
+/* Latency (cluster) form of the NTT blind rotation: one thread-block cluster
+ * of k+1 CTAs per gate, CTA j owning accumulator polynomial j, so a gate's
+ * CMux chain runs about (k+2)/2 times faster while the GPU has SMs to spare.
+ * MK_CLUSTER_AUTO (default) uses it for launches of at most
+ * SM count / (k+1) gates for k <= 2 and 2 * SM count / (k+1) for k >= 3
+ * (50, 60 and 38 gates at k = 2, 4 and 7 on 152 SMs); _ON for every
+ * launch, _OFF never.  Only the
+ * NTT forms with k <= 7; results are bit-identical either way.  No paper
+ * counterpart: a scheduling choice. */
+enum { MK_CLUSTER_AUTO = 0, MK_CLUSTER_OFF = 1, MK_CLUSTER_ON = 2 };
+int mk_ctx_set_cluster(mk_ctx *ctx, int mode);
+
 /* The k-bit operators evaluate their netlist level by level.  With graphs on
  * (the default) the level loop of each (operator, width, pairs) plan is
  * captured once as a CUDA graph on a stream the context owns and replayed on

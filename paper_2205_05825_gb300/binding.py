@@ -19,6 +19,7 @@ GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
 PRESETS = {"toy": 0, "full": 1, "paper": 2}
 NUM_VARIANTS = 4
 FORMS = {"ntt": 0, "ntt2": 1, "fft": 2, "tc": 3}
+CLUSTER_MODES = {"auto": 0, "off": 1, "on": 2}
 
 U32P = ctypes.POINTER(ctypes.c_uint32)
 U8P = ctypes.POINTER(ctypes.c_uint8)
@@ -86,6 +87,7 @@ _SIGS = {
     "mk_autotune": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]),
     "mk_ctx_set_graphs": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_ctx_set_cluster": (ctypes.c_int, [VP, ctypes.c_int]),
     "mk_autotune_form": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
     "mk_add_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
@@ -232,6 +234,10 @@ class Context:
         ms = (ctypes.c_float * NUM_VARIANTS)()
         self._check(self.L.mk_autotune(self.h, sample_gates, ctypes.byref(best), ms), "mk_autotune")
         return best.value, list(ms)
+
+    def set_cluster(self, mode):
+        """Latency (cluster) kernel: "auto" (small launches), "on" or "off"."""
+        self._check(self.L.mk_ctx_set_cluster(self.h, CLUSTER_MODES[mode]), "mk_ctx_set_cluster")
 
     def set_graphs(self, on):
         """Replay each operator's level loop as a captured CUDA graph (default on)."""

@@ -24,8 +24,12 @@ CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu", "mk_tensor.cu"]
 BR_SOURCE = "mk_br.cu"
 BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(4)] + \
     [(logn, 2, 0) for logn in (8, 10)]
+# mk_brc.cu (the cluster kernel) is compiled once per (log2 N, field).
+BRC_SOURCE = "mk_brc.cu"
+BRC_INSTANCES = [(logn, f) for logn in (8, 10) for f in (0, 1)]
 CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp", "mk_server.cpp"]
-HEADERS = ["mk_internal.h", "mk_ctx.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", BR_SOURCE]
+HEADERS = ["mk_internal.h", "mk_ctx.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", "mk_bootstrap_cluster.cuh",
+           BR_SOURCE, BRC_SOURCE]
 
 
 def _newest_input():
@@ -52,6 +56,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                "-DMK_LOGN=%d" % logn, "-DMK_FIELD=%d" % f, "-DMK_VARIANT=%d" % v, *ptxas_v, "-c",
                os.path.join(CSRC, BR_SOURCE), "-o", obj]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        objs.append(obj)
+    for logn, f in BRC_INSTANCES:
+        obj = os.path.join(OUT_DIR, "mk_brc_%d_f%d.o" % (logn, f))
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+               "-DMK_LOGN=%d" % logn, "-DMK_FIELD=%d" % f, *ptxas_v, "-c", os.path.join(CSRC, BRC_SOURCE), "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs.append(obj)
     for src in CPP_SOURCES:

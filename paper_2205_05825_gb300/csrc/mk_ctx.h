@@ -273,6 +273,7 @@ struct CircuitPlan {
     // The level loop captured as a CUDA graph, and what it was captured with.
     cudaGraphExec_t graph = nullptr;
     int graph_form = -1, graph_variant = -1;
+    uint32_t graph_cluster = 0;
     DeviceKeys graph_keys{};
     ~CircuitPlan() {
         if (graph) cudaGraphExecDestroy(graph);
@@ -312,6 +313,8 @@ struct mk_ctx {
     // measurement: event pairs around launches, per kernel class
     bool timing = false;
     bool use_graphs = true;               // circuits replay their level loop as a CUDA graph
+    int cluster_mode = MK_CLUSTER_AUTO;   // latency (cluster) kernel for small batches
+    uint32_t sm_count = 0;
     cudaStream_t capture_stream = nullptr;  // non-default stream the graphs are captured on
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
     std::vector<cudaEvent_t> ev_pool;
@@ -323,7 +326,14 @@ struct mk_ctx {
     size_t bk_words() const { return (size_t)P.n * 3 * P.d * P.N; }
     size_t ks_words() const { return (size_t)P.N * P.t * ((1u << P.ks_bit) - 1) * (P.n + 1); }
     LaunchShape shape() const {
-        return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form};
+        // AUTO: the cluster kernel while the launch's clusters need at most one
+        // CTA per SM (k <= 2) or two (k >= 3, where a gate's chain shortens
+        // more); beyond that the batched kernel's throughput wins.  Measured
+        // crossover on GB300: k = 2 at ~50 gates, k = 4 above 50, k = 7 above 30.
+        const uint32_t cmax = cluster_mode == MK_CLUSTER_ON ? 0xFFFFFFFFu
+                              : cluster_mode == MK_CLUSTER_OFF ? 0u
+                                                               : (P.k <= 2 ? 1u : 2u) * sm_count / (P.k + 1);
+        return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form, cmax};
     }
     DeviceKeys dkeys() const {
         // twiddles: [2][N] of 8-byte (NTT) or 16-byte (NTT2) entries; FFT: one [3][N/2] table

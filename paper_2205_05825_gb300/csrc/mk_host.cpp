@@ -418,6 +418,7 @@ void capture_levels(mk_ctx *c, CircuitPlan *pl, const LaunchShape &S, const Devi
     if (pl->graph) {
         pl->graph_form = c->form;
         pl->graph_variant = c->variant;
+        pl->graph_cluster = S.cluster_max;
         pl->graph_keys = K;
     }
 }
@@ -449,6 +450,7 @@ int run_circuit(mk_ctx *c, int op, uint32_t k, const uint32_t *d_a, const uint32
     bool replayed = false;
     if (e == cudaSuccess && c->use_graphs && !c->timing && c->form != MK_FORM_TC) {
         if (pl->graph && (pl->graph_form != c->form || pl->graph_variant != c->variant ||
+                          pl->graph_cluster != S.cluster_max ||
                           std::memcmp(&pl->graph_keys, &K, sizeof(K)) != 0)) {
             cudaGraphExecDestroy(pl->graph);
             pl->graph = nullptr;
@@ -589,6 +591,9 @@ int mk_ctx_create(const mk_params *params, uint64_t crs_seed, int device, void *
             delete c;
             return MK_EDEVICE;
         }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+            c->sm_count = (uint32_t)sms;
     }
     *out = c;
     return MK_OK;
@@ -635,6 +640,14 @@ int mk_ctx_set_form(mk_ctx *c, int form) {
 int mk_ctx_get_form(const mk_ctx *c, int *form) {
     if (!c || !form) return MK_EINVAL;
     *form = c->form;
+    return MK_OK;
+}
+
+int mk_ctx_set_cluster(mk_ctx *c, int mode) {
+    if (!c) return MK_EINVAL;
+    if (mode != MK_CLUSTER_AUTO && mode != MK_CLUSTER_OFF && mode != MK_CLUSTER_ON)
+        return fail(c, MK_EINVAL, "cluster mode must be MK_CLUSTER_AUTO, _OFF or _ON");
+    c->cluster_mode = mode;
     return MK_OK;
 }
 

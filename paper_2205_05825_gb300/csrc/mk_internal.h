@@ -49,6 +49,9 @@ struct LaunchShape {
     uint32_t n, N, logN, k, d, bg_bit, ks_bit, t;
     int variant;  // blind-rotation variant (see kVariantNpf)
     int form;     // MK_FORM_*
+    // Batches of at most this many gates run the cluster (latency) kernel of
+    // the NTT forms: one CTA per accumulator polynomial (0: never).
+    uint32_t cluster_max;
 };
 
 // a1-a8: linear part, window shift, modulus switch, blind rotation (NTT form),
@@ -96,6 +99,19 @@ MK_DECLARE_BOOTSTRAP_F(10, 0)
 MK_DECLARE_BOOTSTRAP_F(10, 1)
 MK_DECLARE_BOOTSTRAP(8, 2, 0)
 MK_DECLARE_BOOTSTRAP(10, 2, 0)
+
+// Cluster (latency) form of the NTT blind rotation, one translation unit per
+// (ring dimension, field): mk_brc.cu built with -DMK_LOGN -DMK_FIELD.  Same
+// arguments as the launchers above; needs k + 1 <= 8.
+#define MK_DECLARE_CLUSTER(LOGN, F)                                                                            \
+    cudaError_t launch_cluster_logn##LOGN##_f##F(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc, \
+                                                 const uint32_t *ct_a, const uint32_t *ct_b,                    \
+                                                 const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,     \
+                                                 uint32_t *acc_out, uint32_t count, cudaStream_t st);
+MK_DECLARE_CLUSTER(8, 0)
+MK_DECLARE_CLUSTER(8, 1)
+MK_DECLARE_CLUSTER(10, 0)
+MK_DECLARE_CLUSTER(10, 1)
 
 // MK_FORM_TC (mk_tensor.cu): the blind rotation of a batch as a wave of
 // tensor-core Toeplitz products.  Same arguments as the launchers above;

@@ -375,6 +375,14 @@ BootstrapFn pick(const LaunchShape &S) {
     if (S.logN == 10) return t10[S.form][S.variant];
     return nullptr;
 }
+
+// The cluster (latency) launcher for this shape and batch, or nullptr.
+BootstrapFn pick_cluster(const LaunchShape &S, uint32_t count) {
+    if (count > S.cluster_max || S.k + 1 > 8 || (S.form != MK_FORM_NTT && S.form != MK_FORM_NTT2)) return nullptr;
+    if (S.logN == 8) return S.form == MK_FORM_NTT ? launch_cluster_logn8_f0 : launch_cluster_logn8_f1;
+    if (S.logN == 10) return S.form == MK_FORM_NTT ? launch_cluster_logn10_f0 : launch_cluster_logn10_f1;
+    return nullptr;
+}
 }  // namespace
 
 cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
@@ -382,6 +390,7 @@ cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, cons
                                  cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     if (S.form == MK_FORM_TC) return launch_bootstrap_tc(S, K, desc, ct_a, ct_b, nullptr, -1, ext, nullptr, count, st);
+    if (BootstrapFn fc = pick_cluster(S, count)) return fc(S, K, desc, ct_a, ct_b, nullptr, -1, ext, nullptr, count, st);
     BootstrapFn f = pick(S);
     if (!f) return cudaErrorInvalidValue;
     return f(S, K, desc, ct_a, ct_b, nullptr, -1, ext, nullptr, count, st);
@@ -391,6 +400,8 @@ cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, c
                                     uint32_t count, int64_t max_steps, uint32_t *acc, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     if (S.form == MK_FORM_TC) return launch_bootstrap_tc(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);
+    if (BootstrapFn fc = pick_cluster(S, count))
+        return fc(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);
     BootstrapFn f = pick(S);
     if (!f) return cudaErrorInvalidValue;
     return f(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);

@@ -88,6 +88,8 @@ def main():
     ap.add_argument("--loads", default="0.5,0.9")
     ap.add_argument("--wave-gates", type=int, default=4096)
     ap.add_argument("--toy", action="store_true")
+    ap.add_argument("--cluster", default="auto", choices=["auto", "on", "off"],
+                    help="latency (cluster) blind rotation for small waves")
     args = ap.parse_args()
     B.load(build_if_missing=True)
     P = W.toy_params(args.parties) if args.toy else W.full_params(args.parties)
@@ -95,6 +97,7 @@ def main():
     for i, s in enumerate(W.party_seeds(args.parties)):
         ctx.keygen(i, s)
     ctx.autotune(1024)
+    ctx.set_cluster(args.cluster)
     server = B.Server(ctx, wave_gates=args.wave_gates, pool_rows=1 << 20)
     client = Client(ctx, args.bits)
     stream = W.gd_request_stream(max(args.capacity_requests, args.requests), bits=args.bits)
@@ -108,7 +111,7 @@ def main():
     lat, wall = run_stream(server, client, reqs)
     capacity = len(reqs) / wall
     ok = all(client.result(r) == W.expected_result(r["op"], r["a"], r["b"], args.bits) for r in reqs)
-    out = {"parties": args.parties, "bits": args.bits, "n": P["n"], "N": P["N"], "mix": mix,
+    out = {"parties": args.parties, "bits": args.bits, "n": P["n"], "N": P["N"], "mix": mix, "cluster": args.cluster,
            "capacity_requests_per_s": capacity, "capacity_wall_s": wall, "decrypt_ok": ok, "loads": []}
     for load in [float(x) for x in args.loads.split(",") if x]:
         reqs = build(args.requests, offset=10000)

@@ -198,6 +198,7 @@ def test_toy_every_variant_bit_exact(toy, form, variant):
     P, keys, ctx, g, b1, b2, c1, c2 = toy
     ctx.set_form(form)
     ctx.set_variant(variant)
+    ctx.set_cluster("off")  # the batched kernel's variants, not the latency form
     try:
         out = torch.zeros((len(g), ctx.W), dtype=torch.int32, device="cuda")
         ctx.gates(to_dev(g.astype(np.uint8)), to_dev(c1), to_dev(c2), out)
@@ -211,6 +212,7 @@ def test_toy_every_variant_bit_exact(toy, form, variant):
     finally:
         ctx.set_form("ntt2")
         ctx.set_variant(2)
+        ctx.set_cluster("auto")
 
 
 @pytest.mark.parametrize("form,variant", FORM_VARIANTS)
@@ -227,6 +229,7 @@ def test_full_k2_every_variant_sampled(full2, form, variant):
     c2 = o.encrypt(P, keys, 1, b2, W.encryption_seed(7, 1))
     ctx.set_form(form)
     ctx.set_variant(variant)
+    ctx.set_cluster("off")
     try:
         out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
         ctx.gates(to_dev(types.astype(np.uint8)), to_dev(c1), to_dev(c2), out)
@@ -234,6 +237,7 @@ def test_full_k2_every_variant_sampled(full2, form, variant):
     finally:
         ctx.set_form("ntt2")
         ctx.set_variant(2)
+        ctx.set_cluster("auto")
     exp = np.array([TRUTH[int(t)](int(x), int(y)) for t, x, y in zip(types, b1, b2)], np.uint8)
     assert np.array_equal(o.decrypt(P, keys, got), exp)
     idx = np.array([0, 50, 95])
@@ -275,3 +279,59 @@ def test_toy_keyswitch_batch_boundaries(toy, count):
     out = torch.zeros((count, ctx.W), dtype=torch.int32, device="cuda")
     ctx.stage_keyswitch(to_dev(ext), out)
     assert np.array_equal(from_dev(out), o.keyswitch(P, keys, ext))
+
+
+@pytest.mark.parametrize("form", ["ntt", "ntt2"])
+def test_toy_cluster_form_stages_bit_exact(toy, form):
+    """The latency (cluster) form of the blind rotation, forced on: blind
+    rotation after 0, 1, 2, 37 and all steps, whole gates, word for word."""
+    import torch
+    from oracle import oracle as o
+    P, keys, ctx, g, b1, b2, c1, c2 = toy
+    ctx.set_form(form)
+    ctx.set_cluster("on")
+    try:
+        lins = np.stack([o.gate_linear(P, int(t), x, y) for t, x, y in zip(g, c1, c2)])
+        ref_abar = o.modswitch_input(P, lins)
+        abar = to_dev(ref_abar)
+        for steps in (0, 1, 2, 37, -1):
+            acc = torch.zeros((len(g), 3, P["N"]), dtype=torch.int32, device="cuda")
+            ctx.stage_blind_rotate(abar, steps, acc)
+            assert np.array_equal(from_dev(acc), o.blind_rotate(P, keys, ref_abar, max_steps=steps)), steps
+        out = torch.zeros((len(g), ctx.W), dtype=torch.int32, device="cuda")
+        ctx.gates(to_dev(g.astype(np.uint8)), to_dev(c1), to_dev(c2), out)
+        assert np.array_equal(from_dev(out), o.gates(P, keys, g, c1, c2))
+    finally:
+        ctx.set_form("ntt2")
+        ctx.set_cluster("auto")
+
+
+@pytest.mark.parametrize("k", [2, 4, 7])
+def test_full_cluster_form_sampled(gpu_ready, k):
+    """Full size, cluster form forced on, joint-key inputs (all k*n steps):
+    every gate decrypts, sampled gates byte-equal to the oracle, and the
+    batched kernel gives the same ciphertexts."""
+    import torch
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.full_params(k)
+    keys = oracle_keys(P)
+    ctx = _ctx(P, keys)
+    G = 16
+    types, b1, b2 = W.random_gates(G, config_id=60 + k)
+    c1 = o.encrypt_joint(P, keys, b1, W.encryption_seed(60 + k, 0))
+    c2 = o.encrypt_joint(P, keys, b2, W.encryption_seed(60 + k, 1))
+    d = (to_dev(types.astype(np.uint8)), to_dev(c1), to_dev(c2))
+    outs = {}
+    for mode in ("on", "off"):
+        ctx.set_cluster(mode)
+        out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
+        ctx.gates(*d, out)
+        outs[mode] = from_dev(out)
+    assert np.array_equal(outs["on"], outs["off"])
+    exp = np.array([TRUTH[int(t)](int(x), int(y)) for t, x, y in zip(types, b1, b2)], np.uint8)
+    assert np.array_equal(o.decrypt(P, keys, outs["on"]), exp)
+    if k <= 4:  # the schoolbook oracle needs minutes per gate beyond that
+        idx = np.array([0])
+        assert np.array_equal(outs["on"][idx], o.gates(P, keys, types[idx], c1[idx], c2[idx]))
+    ctx.close()
