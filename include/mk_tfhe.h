@@ -142,7 +142,7 @@ int mk_ctx_set_graphs(mk_ctx *ctx, int on);
  * synchronises the stream.  MK_FORM_FFT and MK_FORM_TC have one kernel for
  * every variant number: there it times nothing, reports 0 ms and keeps the
  * variant.  No paper counterpart: a tuning aid. */
-#define MK_NUM_VARIANTS 4
+#define MK_NUM_VARIANTS 6
 int mk_ctx_set_variant(mk_ctx *ctx, int variant);
 int mk_ctx_get_variant(const mk_ctx *ctx, int *variant);
 int mk_autotune(mk_ctx *ctx, uint32_t sample_gates, int *best, float *ms_out);

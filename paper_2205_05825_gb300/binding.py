@@ -17,7 +17,7 @@ ERRORS = {-1: "MK_EINVAL", -2: "MK_ENOMEM", -3: "MK_EPARAMS", -4: "MK_ETIMEOUT",
           -6: "MK_ESTATE", -7: "MK_EFORMAT"}
 GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
 PRESETS = {"toy": 0, "full": 1, "paper": 2}
-NUM_VARIANTS = 4
+NUM_VARIANTS = 6
 FORMS = {"ntt": 0, "ntt2": 1, "fft": 2, "tc": 3}
 CLUSTER_MODES = {"auto": 0, "off": 1, "on": 2}
 

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu", "mk_tensor.cu"]
 # mk_br.cu is compiled once per (log2 N, blind-rotation variant).
 BR_SOURCE = "mk_br.cu"
-BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(4)] + \
+BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(6)] + \
     [(logn, 2, 0) for logn in (8, 10)]
 # mk_brc.cu (the cluster kernel) is compiled once per (log2 N, field).
 BRC_SOURCE = "mk_brc.cu"

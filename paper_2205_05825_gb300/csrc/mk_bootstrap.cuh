@@ -195,25 +195,26 @@ struct FieldDual {
     }
 };
 
-template <class E>
-__device__ __forceinline__ void load8(const E *__restrict__ src, E (&v)[8]) {
-    static_assert(sizeof(E) == 8, "8-byte elements");
+// EPT consecutive 8-byte elements (EPT even) through the read-only cache.
+template <int EPT, class E>
+__device__ __forceinline__ void load_ept(const E *__restrict__ src, E (&v)[EPT]) {
+    static_assert(sizeof(E) == 8 && EPT % 2 == 0, "8-byte elements, an even count");
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < EPT / 2; ++q) {
         const uint4 t = __ldg(s4 + q);
         reinterpret_cast<uint4 *>(v)[q] = t;
     }
 }
 
 // ------------------------------------------------------------ negacyclic NTT
-// Thread `tid` (of N/8) holds 8 elements per polynomial.  A pass processes up
-// to three consecutive butterfly stages in registers; its 8 elements are the
-// indices whose bits [LO, LO+3) vary:  j = base(tid, LO) | c << LO with
-// base = tid[0,LO) | tid[LO,..) << (LO+3).
+// Thread `tid` (of T = N/EPT) holds EPT = 2^SB elements per polynomial (8 or
+// 4).  A pass processes up to SB consecutive butterfly stages in registers;
+// its EPT elements are the indices whose bits [LO, LO+SB) vary:
+// j = base(tid, LO) | c << LO with base = tid[0,LO) | tid[LO,..) << (LO+SB).
 // Forward (Cooley-Tukey, twist folded into psi^bitrev): input natural order in
-// layout LO = logN-3 (coefficient tid + (N/8)*c), output bit-reversed order in
-// layout LO = 0 (index 8*tid + c).  Inverse (Gentleman-Sande) goes back, and
+// layout LO = logN-SB (coefficient tid + T*c), output bit-reversed order in
+// layout LO = 0 (index EPT*tid + c).  Inverse (Gentleman-Sande) goes back, and
 // omits the 1/N factor (the keys carry it).  Between passes the elements move
 // through padded shared memory (one pad word every 16 keeps each 64-bit warp
 // access at the 2-wavefront minimum).
@@ -223,13 +224,16 @@ __device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }
 // stride-4 twiddle reads of the late stages hit distinct banks.
 __device__ __forceinline__ int twp(int t) { return t + (t >> 2); }
 
+template <int SB = 3>
 __device__ __forceinline__ int jbase(int tid, int LO) {
-    return (tid & ((1 << LO) - 1)) | ((tid >> LO) << (LO + 3));
+    return (tid & ((1 << LO) - 1)) | ((tid >> LO) << (LO + SB));
 }
+
+constexpr int log2_ept(int ept) { return ept == 8 ? 3 : (ept == 4 ? 2 : 1); }
 
 // TWG: twiddles read from global memory through the read-only cache
 // (unpadded table) instead of a per-CTA shared-memory copy.
-template <class F, int LOGN, bool TWG>
+template <class F, int LOGN, bool TWG, int EPT = 8>
 struct Ntt {
     using E = typename F::E;
     using Tw = typename F::Tw;
@@ -238,16 +242,18 @@ struct Ntt {
         else return tw[twp(t)];
     }
     static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 8;
+    static constexpr int SB = log2_ept(EPT);
+    static_assert(EPT == 8 || EPT == 4, "8 or 4 elements per thread");
+    static constexpr int T = N / EPT;
     static constexpr int PN = N + N / 16;  // padded polynomial stride in xbuf
 
     // Forward stage at bit b (distance 2^b) inside a pass with element bits
-    // [LO, LO+3): element pairs (c, c + D), D = 2^(b - LO).
+    // [LO, LO+SB): element pairs (c, c + D), D = 2^(b - LO).
     template <int NP, int D>
-    __device__ static __forceinline__ void fwd_stage(E (&x)[NP][8], int jb, int LO, int b, const Tw *tw) {
+    __device__ static __forceinline__ void fwd_stage(E (&x)[NP][EPT], int jb, int LO, int b, const Tw *tw) {
         const int m = 1 << (LOGN - 1 - b);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < EPT; ++c) {
             if (c & D) continue;
             const Tw S = twiddle(tw, m + ((jb | (c << LO)) >> (b + 1)));
 #pragma unroll
@@ -256,10 +262,10 @@ struct Ntt {
     }
 
     template <int NP, int D>
-    __device__ static __forceinline__ void inv_stage(E (&x)[NP][8], int jb, int LO, int b, const Tw *tw) {
+    __device__ static __forceinline__ void inv_stage(E (&x)[NP][EPT], int jb, int LO, int b, const Tw *tw) {
         const int m = 1 << (LOGN - 1 - b);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < EPT; ++c) {
             if (c & D) continue;
             const Tw S = twiddle(tw, m + ((jb | (c << LO)) >> (b + 1)));
 #pragma unroll
@@ -268,50 +274,54 @@ struct Ntt {
     }
 
     template <int NP>
-    __device__ static __forceinline__ void exchange(E (&x)[NP][8], int tid, E *buf, int LOf, int LOt) {
-        const int bf = jbase(tid, LOf);
+    __device__ static __forceinline__ void exchange(E (&x)[NP][EPT], int tid, E *buf, int LOf, int LOt) {
+        const int bf = jbase<SB>(tid, LOf);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) buf[p * PN + pidx(bf | (c << LOf))] = x[p][c];
+            for (int c = 0; c < EPT; ++c) buf[p * PN + pidx(bf | (c << LOf))] = x[p][c];
         __syncthreads();
-        const int bt = jbase(tid, LOt);
+        const int bt = jbase<SB>(tid, LOt);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) x[p][c] = buf[p * PN + pidx(bt | (c << LOt))];
+            for (int c = 0; c < EPT; ++c) x[p][c] = buf[p * PN + pidx(bt | (c << LOt))];
         __syncthreads();
     }
 
-    // natural (layout logN-3) -> bit-reversed (layout 0)
+    // natural (layout logN-SB) -> bit-reversed (layout 0)
     template <int NP>
-    __device__ static __forceinline__ void forward(E (&x)[NP][8], int tid, const Tw *tw, E *buf) {
-        int prev = LOGN - 3;
+    __device__ static __forceinline__ void forward(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf) {
+        int prev = LOGN - SB;
 #pragma unroll 1
-        for (int hi = LOGN - 1; hi >= 0; hi -= 3) {
-            const int LO = hi >= 2 ? hi - 2 : 0;
+        for (int hi = LOGN - 1; hi >= 0; hi -= SB) {
+            const int LO = hi >= SB - 1 ? hi - (SB - 1) : 0;
             if (LO != prev) exchange<NP>(x, tid, buf, prev, LO);
-            const int jb = jbase(tid, LO);
-            if (hi - LO == 2) fwd_stage<NP, 4>(x, jb, LO, LO + 2, tw);
+            const int jb = jbase<SB>(tid, LO);
+            if constexpr (SB == 3) {
+                if (hi - LO == 2) fwd_stage<NP, 4>(x, jb, LO, LO + 2, tw);
+            }
             if (hi - LO >= 1) fwd_stage<NP, 2>(x, jb, LO, LO + 1, tw);
             fwd_stage<NP, 1>(x, jb, LO, LO, tw);
             prev = LO;
         }
     }
 
-    // bit-reversed (layout 0) -> natural (layout logN-3), without 1/N
+    // bit-reversed (layout 0) -> natural (layout logN-SB), without 1/N
     template <int NP>
-    __device__ static __forceinline__ void inverse(E (&x)[NP][8], int tid, const Tw *tw, E *buf) {
+    __device__ static __forceinline__ void inverse(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf) {
         int prev = 0;
 #pragma unroll 1
-        for (int lo = 0; lo < LOGN; lo += 3) {
-            const int hi = (lo + 2 < LOGN - 1) ? lo + 2 : LOGN - 1;
-            const int LO = (lo < LOGN - 3) ? lo : LOGN - 3;
+        for (int lo = 0; lo < LOGN; lo += SB) {
+            const int hi = (lo + SB - 1 < LOGN - 1) ? lo + SB - 1 : LOGN - 1;
+            const int LO = (lo < LOGN - SB) ? lo : LOGN - SB;
             if (LO != prev) exchange<NP>(x, tid, buf, prev, LO);
-            const int jb = jbase(tid, LO);
+            const int jb = jbase<SB>(tid, LO);
             if (lo == LO) inv_stage<NP, 1>(x, jb, LO, LO, tw);
             if (lo <= LO + 1 && hi >= LO + 1) inv_stage<NP, 2>(x, jb, LO, LO + 1, tw);
-            if (hi == LO + 2) inv_stage<NP, 4>(x, jb, LO, LO + 2, tw);
+            if constexpr (SB == 3) {
+                if (hi == LO + 2) inv_stage<NP, 4>(x, jb, LO, LO + 2, tw);
+            }
             prev = LO;
         }
     }
@@ -363,13 +373,20 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
     return L;
 }
 
+// A += x * key over EPT elements; key words at key + EPT*tid (layout 0).
+template <class F, int EPT>
+__device__ __forceinline__ void mac_ept(typename F::E (&A)[EPT], const typename F::E (&x)[EPT],
+                                        const typename F::E *__restrict__ key, int tid) {
+    typename F::E kv[EPT];
+    load_ept<EPT>(key + tid * EPT, kv);
+#pragma unroll
+    for (int c = 0; c < EPT; ++c) F::mac(A[c], x[c], kv[c]);
+}
+
 template <class F>
 __device__ __forceinline__ void mac8(typename F::E (&A)[8], const typename F::E (&x)[8],
                                      const typename F::E *__restrict__ key, int tid) {
-    typename F::E kv[8];
-    load8(key + tid * 8, kv);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) F::mac(A[c], x[c], kv[c]);
+    mac_ept<F, 8>(A, x, key, tid);
 }
 
 // One CMux step for party i (1..k) at rotation e:
@@ -377,34 +394,34 @@ __device__ __forceinline__ void mac8(typename F::E (&A)[8], const typename F::E 
 // Slots q = 0..k are the accumulator polynomials in the order 0, i, others
 // (phase A); slot k+1 is phase B (w = g^-1(v) against f0, f1).  NPF digit
 // polynomials go through one forward transform together.
-template <class F, int LOGN, int NPF, bool TWG>
+template <class F, int LOGN, int NPF, bool TWG, int EPT>
 __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys &K, const Gadget &G,
                                           const typename F::E *bk, int i, uint32_t e, uint32_t *acc,
                                           typename F::E *xbuf, const typename F::Tw *twf,
                                           const typename F::Tw *twi, int tid) {
-    using NT = Ntt<F, LOGN, TWG>;
+    using NT = Ntt<F, LOGN, TWG, EPT>;
     using E = typename F::E;
     constexpr int N = NT::N, T = NT::T;
     const int k = (int)S.k;
     const E *keyA = static_cast<const E *>(K.keyA);
-    E C0[8], CI[8], CJ[8], V[8];
-    uint32_t vv[8];
+    E C0[EPT], CI[EPT], CJ[EPT], V[EPT];
+    uint32_t vv[EPT];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) C0[c] = CI[c] = CJ[c] = V[c] = F::zero();
+    for (int c = 0; c < EPT; ++c) C0[c] = CI[c] = CJ[c] = V[c] = F::zero();
 #pragma unroll 1
     for (int q = 0; q <= k + 1; ++q) {
         const int jj = (q == 0) ? 0 : (q == 1 ? i : (q - 1 < i ? q - 1 : q));  // q <= k only
         if (q >= 2 && q <= k) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) CJ[c] = F::zero();
+            for (int c = 0; c < EPT; ++c) CJ[c] = F::zero();
         }
 #pragma unroll 1
         for (int l0 = 0; l0 < 3; l0 += NPF) {
-            E x[NPF][8];
+            E x[NPF][EPT];
             if (q <= k) {
                 const uint32_t *ap = acc + jj * N;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < EPT; ++c) {
                     const uint32_t m = tid + T * c;
                     uint32_t r = m + e;
                     if (r >= 2 * N) r -= 2 * N;
@@ -416,7 +433,7 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
+                for (int c = 0; c < EPT; ++c)
 #pragma unroll
                     for (int p = 0; p < NPF; ++p) x[p][c] = F::from_digit(G.digit(vv[c], l0 + p));
             }
@@ -427,13 +444,13 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
                 if (q <= k) {
                     const E *kd = bk + l * N;                              // d_l of BK_{i,j}
                     const E *ka = keyA + ((size_t)jj * 3 + l) * N;         // -a_l or pk_jj[l]
-                    if (q == 0) mac8<F>(C0, x[p], kd, tid);
-                    else if (q == 1) mac8<F>(CI, x[p], kd, tid);
-                    else mac8<F>(CJ, x[p], kd, tid);
-                    mac8<F>(V, x[p], ka, tid);
+                    if (q == 0) mac_ept<F, EPT>(C0, x[p], kd, tid);
+                    else if (q == 1) mac_ept<F, EPT>(CI, x[p], kd, tid);
+                    else mac_ept<F, EPT>(CJ, x[p], kd, tid);
+                    mac_ept<F, EPT>(V, x[p], ka, tid);
                 } else {
-                    mac8<F>(C0, x[p], bk + (3 + l) * N, tid);  // f0_l
-                    mac8<F>(CI, x[p], bk + (6 + l) * N, tid);  // f1_l
+                    mac_ept<F, EPT>(C0, x[p], bk + (3 + l) * N, tid);  // f0_l
+                    mac_ept<F, EPT>(CI, x[p], bk + (6 + l) * N, tid);  // f1_l
                 }
             }
         }
@@ -445,44 +462,44 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
         const bool single = (q >= 2 && q < k) || (q == k && k == 1);
         if (pair) {
             const bool last = (q == k + 1);
-            E y[2][8];
+            E y[2][EPT];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < EPT; ++c) {
                 y[0][c] = last ? C0[c] : CJ[c];
                 y[1][c] = last ? CI[c] : V[c];
             }
             NT::template inverse<2>(y, tid, twi, xbuf);
             uint32_t *d0 = acc + (last ? 0 : jj) * N;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) d0[tid + T * c] += F::to_u32(y[0][c]);
+            for (int c = 0; c < EPT; ++c) d0[tid + T * c] += F::to_u32(y[0][c]);
             if (last) {
                 uint32_t *d1 = acc + i * N;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) d1[tid + T * c] += F::to_u32(y[1][c]);
+                for (int c = 0; c < EPT; ++c) d1[tid + T * c] += F::to_u32(y[1][c]);
             } else {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) vv[c] = F::to_u32(y[1][c]);
+                for (int c = 0; c < EPT; ++c) vv[c] = F::to_u32(y[1][c]);
             }
         } else if (single) {
             const bool is_v = (q == k);
-            E y[1][8];
+            E y[1][EPT];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) y[0][c] = is_v ? V[c] : CJ[c];
+            for (int c = 0; c < EPT; ++c) y[0][c] = is_v ? V[c] : CJ[c];
             NT::template inverse<1>(y, tid, twi, xbuf);
             if (is_v) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) vv[c] = F::to_u32(y[0][c]);
+                for (int c = 0; c < EPT; ++c) vv[c] = F::to_u32(y[0][c]);
             } else {
                 uint32_t *dst = acc + jj * N;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) dst[tid + T * c] += F::to_u32(y[0][c]);
+                for (int c = 0; c < EPT; ++c) dst[tid + T * c] += F::to_u32(y[0][c]);
             }
         }
     }
 }
 
 // k*n CMux steps (i = 1..k, j = 0..n-1 ascending).
-template <class F, int LOGN, int NPF, bool TWG>
+template <class F, int LOGN, int NPF, bool TWG, int EPT>
 __device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const DeviceKeys &K, const uint16_t *abar,
                                                   uint32_t *acc, typename F::E *xbuf, const typename F::Tw *twf,
                                                   const typename F::Tw *twi, int64_t max_steps, int tid) {
@@ -501,16 +518,16 @@ __device__ __forceinline__ void blind_rotate_core(const LaunchShape &S, const De
             const uint32_t e = abar[(i - 1) * n + j];
             if (e == 0) continue;  // X^0 - 1 = 0: every digit is 0, HP adds nothing
             const E *bk = bk_all + ((size_t)((i - 1) * n + j) * 9) * N;
-            cmux_step<F, LOGN, NPF, TWG>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
+            cmux_step<F, LOGN, NPF, TWG, EPT>(S, K, G, bk, i, e, acc, xbuf, twf, twi, tid);
             __syncthreads();
         }
     }
 }
 
-template <class F, int LOGN>
+template <class F, int LOGN, int EPT>
 __device__ __forceinline__ void load_twiddles(const DeviceKeys &K, typename F::Tw *twf, typename F::Tw *twi,
                                               int tid) {
-    constexpr int N = 1 << LOGN, T = N / 8;
+    constexpr int N = 1 << LOGN, T = N / EPT;
     const typename F::Tw *gf = static_cast<const typename F::Tw *>(K.tw_fwd);
     const typename F::Tw *gi = static_cast<const typename F::Tw *>(K.tw_inv);
     for (int x = tid; x < N; x += T) {
@@ -519,11 +536,11 @@ __device__ __forceinline__ void load_twiddles(const DeviceKeys &K, typename F::T
     }
 }
 
-template <int LOGN>
+template <int LOGN, int EPT>
 __device__ __forceinline__ void init_acc(uint32_t *acc, uint32_t k, uint32_t bbar, int tid) {
-    constexpr int N = 1 << LOGN, T = N / 8;
+    constexpr int N = 1 << LOGN, T = N / EPT;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < EPT; ++c) {
         const uint32_t m = tid + T * c;
         uint32_t r = m + bbar;
         if (r >= 2 * N) r -= 2 * N;
@@ -546,9 +563,9 @@ __device__ __forceinline__ void lin_modswitch(const LaunchShape &S, const GateDe
     }
 }
 
-template <int LOGN>
+template <int LOGN, int T>
 __device__ __forceinline__ void sample_extract(const LaunchShape &S, const uint32_t *acc, uint32_t *dst, int tid) {
-    constexpr int N = 1 << LOGN, T = N / 8;
+    constexpr int N = 1 << LOGN;
     for (uint32_t i = 1; i <= S.k; ++i) {
         const uint32_t *ci = acc + i * N;
         uint32_t *ai = dst + (i - 1) * N;
@@ -561,13 +578,13 @@ __device__ __forceinline__ void sample_extract(const LaunchShape &S, const uint3
 //   abar_in == nullptr: linear part + window shift + modulus switch from desc;
 //   otherwise the mod-switched words are read from abar_in.
 //   acc_out == nullptr: SampleExtract + 1/8 into ext; otherwise the raw ACC.
-template <class F, int LOGN, int NPF, int MINB, bool TWG>
-__global__ void __launch_bounds__((1 << LOGN) / 8, MINB)
+template <class F, int LOGN, int NPF, int MINB, bool TWG, int EPT>
+__global__ void __launch_bounds__((1 << LOGN) / EPT, MINB)
 bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
                      const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
                      const uint32_t *__restrict__ abar_in, int64_t max_steps,
                      uint32_t *__restrict__ ext, uint32_t *__restrict__ acc_out) {
-    constexpr int N = 1 << LOGN, T = N / 8;
+    constexpr int N = 1 << LOGN, T = N / EPT;
     using E = typename F::E;
     using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -580,7 +597,7 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
     } else {
         twf = reinterpret_cast<Tw *>(smem + L.twf);
         twi = reinterpret_cast<Tw *>(smem + L.twi);
-        load_twiddles<F, LOGN>(K, reinterpret_cast<Tw *>(smem + L.twf), reinterpret_cast<Tw *>(smem + L.twi), tid);
+        load_twiddles<F, LOGN, EPT>(K, reinterpret_cast<Tw *>(smem + L.twf), reinterpret_cast<Tw *>(smem + L.twi), tid);
     }
     E *xbuf = reinterpret_cast<E *>(smem + L.xbuf);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
@@ -592,28 +609,28 @@ bootstrap_ntt_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ d
         lin_modswitch(S, desc[blockIdx.x], ct_a, ct_b, abar, tid, T);
     }
     __syncthreads();
-    init_acc<LOGN>(acc, S.k, abar[S.k * S.n], tid);
+    init_acc<LOGN, EPT>(acc, S.k, abar[S.k * S.n], tid);
     __syncthreads();
-    blind_rotate_core<F, LOGN, NPF, TWG>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
+    blind_rotate_core<F, LOGN, NPF, TWG, EPT>(S, K, abar, acc, xbuf, twf, twi, max_steps, tid);
     __syncthreads();
     if (acc_out) {
         uint32_t *dst = acc_out + (size_t)blockIdx.x * (S.k + 1) * N;
         for (uint32_t x = tid; x < (S.k + 1) * N; x += T) dst[x] = acc[x];
     } else {
-        sample_extract<LOGN>(S, acc, ext + (size_t)blockIdx.x * (S.k * N + 1), tid);
+        sample_extract<LOGN, T>(S, acc, ext + (size_t)blockIdx.x * (S.k * N + 1), tid);
     }
 }
 
-template <class F, int LOGN, int NPF, int MINB, bool TWG>
+template <class F, int LOGN, int NPF, int MINB, bool TWG, int EPT>
 cudaError_t launch_bootstrap(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                              const uint32_t *ct_a, const uint32_t *ct_b, const uint32_t *abar_in,
                              int64_t max_steps, uint32_t *ext, uint32_t *acc_out, uint32_t count,
                              cudaStream_t st) {
     const SmemLayout L = smem_layout<F, LOGN, NPF, TWG>(S.k, S.n);
-    auto kern = bootstrap_ntt_kernel<F, LOGN, NPF, MINB, TWG>;
+    auto kern = bootstrap_ntt_kernel<F, LOGN, NPF, MINB, TWG, EPT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
-    kern<<<count, (1 << LOGN) / 8, L.total, st>>>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);
+    kern<<<count, (1 << LOGN) / EPT, L.total, st>>>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);
     return cudaGetLastError();
 }
 

@@ -22,10 +22,12 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
     constexpr int NPF = kVariantNpf[MK_VARIANT];
     constexpr int MINB = kVariantMinBlocks[MK_VARIANT];
     constexpr bool TWG = kVariantTwg[MK_VARIANT] != 0;
+    constexpr int EPT = kVariantEpt[MK_VARIANT];
 #if MK_FIELD == 2
     (void)NPF;
     (void)MINB;
     (void)TWG;
+    (void)EPT;
     return br::launch_bootstrap_fft<MK_LOGN - 1>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
                                                  st);
 #else
@@ -34,8 +36,8 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
 #else
     using F = br::FieldDual;
 #endif
-    return br::launch_bootstrap<F, MK_LOGN, NPF, MINB, TWG>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
-                                                            acc_out, count, st);
+    return br::launch_bootstrap<F, MK_LOGN, NPF, MINB, TWG, EPT>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
+                                                                 acc_out, count, st);
 #endif
 }
 }  // namespace mk

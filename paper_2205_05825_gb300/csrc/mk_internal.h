@@ -71,13 +71,18 @@ cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, c
                                     cudaStream_t st);
 
 // Blind-rotation variants: digit polynomials per forward transform (1 or 3),
-// the minimum resident CTAs per SM the register allocation is capped for, and
+// the minimum resident CTAs per SM the register allocation is capped for,
 // where the twiddles live (0: a shared-memory copy per CTA, 1: global memory
-// through the read-only cache).  All give identical results.
-constexpr int kNumVariants = 4;
-constexpr int kVariantNpf[kNumVariants] = {3, 1, 3, 3};
-constexpr int kVariantMinBlocks[kNumVariants] = {3, 4, 3, 4};
-constexpr int kVariantTwg[kNumVariants] = {0, 1, 1, 1};
+// through the read-only cache), and the elements each thread holds per
+// polynomial (8: N/8 threads per gate, three stages per register pass; 4:
+// N/4 threads, two stages per pass, fewer registers per thread).  All give
+// identical results.
+constexpr int kNumVariants = 6;
+constexpr int kVariantNpf[kNumVariants] = {3, 1, 3, 3, 3, 3};
+constexpr int kVariantMinBlocks[kNumVariants] = {3, 4, 3, 4, 2, 3};
+constexpr int kVariantTwg[kNumVariants] = {0, 1, 1, 1, 1, 1};
+constexpr int kVariantEpt[kNumVariants] = {8, 8, 8, 8, 4, 4};
+static_assert(kNumVariants == MK_NUM_VARIANTS, "variant count of the ABI");
 
 // Per-(ring dimension, variant) blind-rotation launchers, one translation unit
 // each (mk_br.cu built with -DMK_LOGN -DMK_VARIANT).  abar_in == nullptr: the
@@ -92,7 +97,7 @@ constexpr int kVariantTwg[kNumVariants] = {0, 1, 1, 1};
                                                           uint32_t count, cudaStream_t st);
 #define MK_DECLARE_BOOTSTRAP_F(LOGN, F)                                                                       \
     MK_DECLARE_BOOTSTRAP(LOGN, F, 0) MK_DECLARE_BOOTSTRAP(LOGN, F, 1) MK_DECLARE_BOOTSTRAP(LOGN, F, 2)          \
-    MK_DECLARE_BOOTSTRAP(LOGN, F, 3)
+    MK_DECLARE_BOOTSTRAP(LOGN, F, 3) MK_DECLARE_BOOTSTRAP(LOGN, F, 4) MK_DECLARE_BOOTSTRAP(LOGN, F, 5)
 MK_DECLARE_BOOTSTRAP_F(8, 0)
 MK_DECLARE_BOOTSTRAP_F(8, 1)
 MK_DECLARE_BOOTSTRAP_F(10, 0)
