@@ -380,13 +380,17 @@ int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters
  *   out[g] = sum_{c < nchunks} keys[c] * digits[c][g]   in Z[X]/(X^N + 1) mod 2^32
  * for g < G.  keys: device uint32 [nchunks][N] (torus32 words); digits:
  * device int8 [nchunks][G][N], each in [-128, 127]; out: device int32
- * [G][N] (the torus32 words, as int32).  N in {256, 1024}, G a positive
- * multiple of 64, 1 <= nchunks <= 3; otherwise MK_EINVAL.  The call
- * allocates a bf16 copy of the digits, runs on `stream` and synchronises it.
+ * [G][N] (the torus32 words, as int32).  engine 0: warp-level mma.sync, G a
+ * positive multiple of 64; engine 1: tcgen05 with TMEM accumulators, G a
+ * positive multiple of 128.  N in {256, 1024}, 1 <= nchunks <= 3; otherwise
+ * MK_EINVAL.  MK_ETIMEOUT if a bounded wait of the tcgen05 kernel gave up.
+ * The call allocates a bf16 copy of the digits, runs on `stream` and
+ * synchronises it.  The same engine numbers select the tensor form's engine
+ * as its variant (mk_ctx_set_variant; mk_autotune times both).
  * No paper counterpart: the negacyclic product of Section 2 (the hybrid
  * product's inner step) isolated for testing the tensor form. */
 int mk_tc_negacyclic(int device, void *stream, uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys,
-                     const int8_t *digits, int32_t *out);
+                     const int8_t *digits, int32_t *out, int engine);
 
 #ifdef __cplusplus
 }

@@ -112,7 +112,7 @@ _SIGS = {
     "mk_measure_butterfly_rate": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_int, ctypes.c_uint32,
                                                  ctypes.POINTER(ctypes.c_double)]),
     "mk_tc_negacyclic": (ctypes.c_int, [ctypes.c_int, VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
-                                        VP, VP, VP]),
+                                        VP, VP, VP, ctypes.c_int]),
 }
 
 _lib = None
@@ -447,14 +447,15 @@ def measure_butterfly_rate(device=0, stream=None, iters=4096, form="ntt"):
     return r.value
 
 
-def tc_negacyclic(keys, digits, out, device=0, stream=None):
+def tc_negacyclic(keys, digits, out, device=0, stream=None, engine=0):
     """out[g] = sum_c keys[c] * digits[c][g] (negacyclic, mod 2^32) by the
-    tensor-form product kernel.  keys: device uint32/int32 [nchunks][N];
-    digits: device int8 [nchunks][G][N]; out: device int32 [G][N]."""
+    tensor-form product kernel (engine 0: mma.sync, 1: tcgen05).  keys:
+    device uint32/int32 [nchunks][N]; digits: device int8 [nchunks][G][N];
+    out: device int32 [G][N]."""
     nch, N = int(keys.shape[0]), int(keys.shape[1])
     G = int(digits.shape[1])
     rc = load().mk_tc_negacyclic(device, ctypes.c_void_p(stream or 0), N, G, nch, _dptr(keys), _dptr(digits),
-                                 _dptr(out))
+                                 _dptr(out), engine)
     if rc != MK_OK:
         raise MkError("mk_tc_negacyclic: %s" % ERRORS.get(rc, rc))
 

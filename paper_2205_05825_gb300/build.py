@@ -19,7 +19,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu", "mk_tensor.cu"]
+CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu", "mk_tensor.cu", "mk_tensor_tc05.cu"]
 # mk_br.cu is compiled once per (log2 N, blind-rotation variant).
 BR_SOURCE = "mk_br.cu"
 BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(6)] + \

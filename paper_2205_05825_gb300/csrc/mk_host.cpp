@@ -680,12 +680,16 @@ int mk_autotune(mk_ctx *c, uint32_t sample_gates, int *best, float *ms_out) {
     if (!c || sample_gates == 0) return MK_EINVAL;
     int rc = device_ready(c, sample_gates);
     if (rc) return rc;
-    if (c->form == MK_FORM_FFT || c->form == MK_FORM_TC) {  // one kernel serves every variant number
+    if (c->form == MK_FORM_FFT) {  // one kernel serves every variant number
         if (ms_out)
             for (int v = 0; v < kNumVariants; ++v) ms_out[v] = 0.f;
         if (best) *best = c->variant;
         return MK_OK;
     }
+    // the tensor form has two engines: variant 0 (mma.sync) and 1 (tcgen05)
+    const int nvar = c->form == MK_FORM_TC ? 2 : kNumVariants;
+    if (ms_out)
+        for (int v = nvar; v < kNumVariants; ++v) ms_out[v] = 0.f;
     const uint32_t cnt = std::min<uint32_t>(sample_gates, c->max_batch);
     uint32_t *d_in = nullptr;
     rc = sample_inputs(c, cnt, &d_in);
@@ -694,7 +698,7 @@ int mk_autotune(mk_ctx *c, uint32_t sample_gates, int *best, float *ms_out) {
     float bestms = 1e30f;
     cudaError_t err = cudaSuccess;
     const int saved = c->variant;
-    for (int v = 0; v < kNumVariants && err == cudaSuccess; ++v) {
+    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
         c->variant = v;
         float ms = 0;
         err = time_sample(c, cnt, d_in, &ms);
@@ -1341,17 +1345,21 @@ int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters
 }
 
 int mk_tc_negacyclic(int device, void *stream, uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys,
-                     const int8_t *digits, int32_t *out) {
-    if (!keys || !digits || !out || (N != 256 && N != 1024) || G == 0 || G % tc_wave_granularity() || nchunks == 0 ||
-        nchunks > 3)
+                     const int8_t *digits, int32_t *out, int engine) {
+    if (!keys || !digits || !out || (N != 256 && N != 1024) || G == 0 || G % (engine == 1 ? 128u : 64u) ||
+        nchunks == 0 || nchunks > 3 || engine < 0 || engine > 1)
         return MK_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return MK_EDEVICE;
     cudaStream_t st = (cudaStream_t)stream;
     void *work = nullptr;
     if (cudaMalloc(&work, (size_t)nchunks * G * N * 2) != cudaSuccess) return MK_ENOMEM;
     int rc = MK_OK;
-    if (launch_negacyclic_tc(N, G, nchunks, keys, digits, out, work, st) != cudaSuccess) rc = MK_EDEVICE;
+    unsigned int timeout = 0;
+    if (engine == 1 && tc05_error(&timeout, true) != cudaSuccess) rc = MK_EDEVICE;
+    if (rc == MK_OK && launch_negacyclic_tc(N, G, nchunks, keys, digits, out, work, engine, st) != cudaSuccess)
+        rc = MK_EDEVICE;
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = MK_EDEVICE;
+    if (rc == MK_OK && engine == 1 && (tc05_error(&timeout, true) != cudaSuccess || timeout != 0)) rc = MK_ETIMEOUT;
     cudaFree(work);
     return rc;
 }

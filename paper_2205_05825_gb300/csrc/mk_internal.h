@@ -125,13 +125,34 @@ cudaError_t launch_bootstrap_tc(const LaunchShape &S, const DeviceKeys &K, const
                                 const uint32_t *ct_b, const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,
                                 uint32_t *acc_out, uint32_t count, cudaStream_t st);
 bool tc_shape_supported(const LaunchShape &S);
+// One pass of a Toeplitz product kernel of the tensor form: output z of the
+// grid's z dimension is dst[type] + (z >> 1) * dst_zstride (row g at
+// g * dst_stride words), type = z & 1, the sum over nchunks products of
+// key[type] + (z >> 1) * key_zstride[type] + c * N (torus32 words) with the
+// digits dig + (z >> 1) * dig_zstride + c * G * N ([G][N] bf16 bit patterns).
+struct TcArgs {
+    int32_t *dst[2];
+    size_t dst_zstride;
+    uint32_t dst_stride;
+    int accumulate;
+    const uint32_t *key[2];
+    size_t key_zstride[2];
+    const uint16_t *dig;
+    size_t dig_zstride;
+    int nchunks;
+};
+// The tcgen05 engine of those products (mk_tensor_tc05.cu): G a multiple of
+// 128.  tc05_error reads (and optionally clears) the timeout record of its
+// bounded waits (0: none).
+cudaError_t launch_products_tc05(const TcArgs &A, uint32_t N, uint32_t G, int outputs, cudaStream_t st);
+cudaError_t tc05_error(unsigned int *code, bool clear);
 constexpr uint32_t kTcWaveGates = 4096;  // gates per wave of the context's workspace
 size_t tc_workspace_bytes(const LaunchShape &S, uint32_t gates);
 uint32_t tc_wave_granularity();
 // out[g] = sum_c keys[c] * digits[c][g] (negacyclic, mod 2^32); work holds
 // nchunks * G * N bf16.
 cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys, const int8_t *digits,
-                                 int32_t *out, void *work, cudaStream_t st);
+                                 int32_t *out, void *work, int engine, cudaStream_t st);
 // Register-resident bf16 m16n8k16 MMA loop: 8 MMAs per warp and iteration.
 cudaError_t launch_mma_peak(uint32_t blocks, uint32_t threads, uint32_t iters, float *sink, cudaStream_t st);
 

@@ -37,6 +37,7 @@ namespace mk {
 namespace {
 
 constexpr int TC_GT = 64;         // gates per CTA tile
+constexpr int TC_PAD = 128;       // waves are padded to this many gates (either engine)
 constexpr int TC_MS = 256;        // output coefficients per CTA tile
 constexpr int TC_THREADS = 256;   // 8 warps: 4 row groups of 64 x 2 gate groups of 32
 
@@ -60,24 +61,6 @@ __device__ __forceinline__ int32_t gadget_digit(uint32_t x, int l, uint32_t bg_b
     const uint32_t xp = x + offset;
     return (int32_t)((xp >> (32 - bg_bit * (l + 1))) & ((1u << bg_bit) - 1)) - (int32_t)(1u << (bg_bit - 1));
 }
-
-// One pass of the product kernel: output z of the grid's z dimension is
-//   dst[type] + (z >> 1) * dst_zstride   (row g at g * dst_stride words),
-// with type = z & 1, and sums nchunks products of
-//   key[type] + (z >> 1) * key_zstride[type] + c * N      (torus32 words)
-// with the digits
-//   dig + (z >> 1) * dig_zstride + c * G * N              ([G][N] bf16).
-struct TcArgs {
-    int32_t *dst[2];
-    size_t dst_zstride;
-    uint32_t dst_stride;
-    int accumulate;
-    const uint32_t *key[2];
-    size_t key_zstride[2];
-    const __nv_bfloat16 *dig;
-    size_t dig_zstride;
-    int nchunks;
-};
 
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[3], uint32_t b0, uint32_t b1) {
     // A registers {a0, a1, a2, a3}; Toeplitz tiles have a3 == a0
@@ -114,7 +97,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_products_kernel(TcArgs A, ui
     const int mw = blockIdx.x * TC_MS + (warp & 3) * 64;  // this warp's 64 output rows
     const int gw = (warp >> 2) * 32;                        // and 32 gates of the tile
     const uint32_t *keyz = type ? A.key[1] + zi * A.key_zstride[1] : A.key[0] + zi * A.key_zstride[0];
-    const __nv_bfloat16 *digz = A.dig + zi * A.dig_zstride + (size_t)g0 * N;
+    const __nv_bfloat16 *digz = reinterpret_cast<const __nv_bfloat16 *>(A.dig) + zi * A.dig_zstride + (size_t)g0 * N;
 
     uint32_t iacc[4][4][4];
 #pragma unroll
@@ -318,6 +301,14 @@ void launch_products(const TcArgs &A, uint32_t G, int outputs, cudaStream_t st) 
     tc_products_kernel<LOGN><<<dim3(N / TC_MS, G / TC_GT, outputs), TC_THREADS, TcSmem<LOGN>::bytes, st>>>(A, G);
 }
 
+// Engine 1: tcgen05 (G a multiple of 128); otherwise warp-level mma.sync.
+template <int LOGN>
+cudaError_t products(int engine, const TcArgs &A, uint32_t G, int outputs, cudaStream_t st) {
+    if (engine == 1) return launch_products_tc05(A, 1u << LOGN, G, outputs, st);
+    launch_products<LOGN>(A, G, outputs, st);
+    return cudaSuccess;
+}
+
 // Workspace carve-up for a wave of Gp gates (multiple of TC_GT).
 struct TcWave {
     uint32_t *abar;       // [Gp][W]
@@ -367,10 +358,11 @@ cudaError_t blind_rotate_wave(const LaunchShape &S, const DeviceKeys &K, const T
         a.key_zstride[0] = 0;
         a.key[1] = keyA;
         a.key_zstride[1] = 3 * (size_t)N;
-        a.dig = w.U;
+        a.dig = reinterpret_cast<const uint16_t *>(w.U);
         a.dig_zstride = 3 * (size_t)Gp * N;
         a.nchunks = 3;
-        launch_products<LOGN>(a, Gp, 2 * (int)(k + 1), st);
+        e = products<LOGN>(S.variant, a, Gp, 2 * (int)(k + 1), st);
+        if (e != cudaSuccess) return e;
         tc_vdigits_kernel<LOGN><<<Gp, 256, 0, st>>>(k, Gp, S.bg_bit, w.V, w.Wd);
         TcArgs b{};
         b.dst[0] = w.C;
@@ -381,10 +373,11 @@ cudaError_t blind_rotate_wave(const LaunchShape &S, const DeviceKeys &K, const T
         b.key[0] = bk + 3 * (size_t)N;
         b.key[1] = bk + 6 * (size_t)N;
         b.key_zstride[0] = b.key_zstride[1] = 0;
-        b.dig = w.Wd;
+        b.dig = reinterpret_cast<const uint16_t *>(w.Wd);
         b.dig_zstride = 0;
         b.nchunks = 3;
-        launch_products<LOGN>(b, Gp, 2, st);
+        e = products<LOGN>(S.variant, b, Gp, 2, st);
+        if (e != cudaSuccess) return e;
         const int next = (step + 1 < steps) ? (int)(step + 1) : -1;
         tc_rotate_digits_kernel<LOGN><<<dim3(Gp, k + 1), 256, 0, st>>>(k, W, Gp, next, 0, S.bg_bit, w.abar, w.acc,
                                                                         w.C, w.U);
@@ -400,7 +393,7 @@ cudaError_t bootstrap_tc(const LaunchShape &S, const DeviceKeys &K, const GateDe
     const uint32_t k = S.k, W = k * S.n + 1, cap = K.tc_ws_gates;
     for (uint32_t start = 0; start < count; start += cap) {
         const uint32_t cnt = count - start < cap ? count - start : cap;
-        const uint32_t Gp = (cnt + TC_GT - 1) / TC_GT * TC_GT;
+        const uint32_t Gp = (cnt + TC_PAD - 1) / TC_PAD * TC_PAD;
         const TcWave w = carve(K.tc_ws, Gp, S);
         cudaError_t e;
         if (abar_in)
@@ -426,12 +419,12 @@ cudaError_t bootstrap_tc(const LaunchShape &S, const DeviceKeys &K, const GateDe
 }  // namespace
 
 size_t tc_workspace_bytes(const LaunchShape &S, uint32_t gates) {
-    const uint32_t Gp = (gates + TC_GT - 1) / TC_GT * TC_GT;
+    const uint32_t Gp = (gates + TC_PAD - 1) / TC_PAD * TC_PAD;
     const size_t W = (size_t)S.k * S.n + 1, poly = (size_t)Gp * (S.k + 1) * S.N;
     return 4 * (((Gp * W + 63) & ~size_t(63)) + 3 * poly) + 2 * (3 * poly + 3 * (size_t)Gp * S.N);
 }
 
-uint32_t tc_wave_granularity() { return TC_GT; }
+uint32_t tc_wave_granularity() { return TC_PAD; }
 
 bool tc_shape_supported(const LaunchShape &S) {
     // exactness needs |digit| * |key byte| * N <= 2^24: digits of at most 8 bits, N <= 1024
@@ -442,14 +435,15 @@ cudaError_t launch_bootstrap_tc(const LaunchShape &S, const DeviceKeys &K, const
                                 const uint32_t *ct_b, const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,
                                 uint32_t *acc_out, uint32_t count, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    if (!tc_shape_supported(S) || !K.tc_ws || K.tc_ws_gates == 0 || K.tc_ws_gates % TC_GT) return cudaErrorInvalidValue;
+    if (!tc_shape_supported(S) || !K.tc_ws || K.tc_ws_gates == 0 || K.tc_ws_gates % TC_PAD) return cudaErrorInvalidValue;
     if (S.N == 256) return bootstrap_tc<8>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count, st);
     return bootstrap_tc<10>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count, st);
 }
 
 cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys, const int8_t *digits,
-                                 int32_t *out, void *work, cudaStream_t st) {
-    if ((N != 256 && N != 1024) || G == 0 || G % TC_GT || nchunks == 0 || nchunks > 3) return cudaErrorInvalidValue;
+                                 int32_t *out, void *work, int engine, cudaStream_t st) {
+    if ((N != 256 && N != 1024) || G == 0 || G % (engine == 1 ? 128 : TC_GT) || nchunks == 0 || nchunks > 3)
+        return cudaErrorInvalidValue;
     __nv_bfloat16 *d = static_cast<__nv_bfloat16 *>(work);
     const size_t total = (size_t)nchunks * G * N;
     tc_int8_to_bf16_kernel<<<1024, 256, 0, st>>>(digits, d, total);
@@ -457,8 +451,9 @@ cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const
     a.dst[0] = a.dst[1] = out;
     a.dst_stride = N;
     a.key[0] = a.key[1] = keys;
-    a.dig = d;
+    a.dig = reinterpret_cast<const uint16_t *>(d);
     a.nchunks = (int)nchunks;
+    if (engine == 1) return launch_products_tc05(a, N, G, 1, st);
     cudaError_t e = N == 256 ? set_products_smem<8>() : set_products_smem<10>();
     if (e != cudaSuccess) return e;
     if (N == 256) launch_products<8>(a, G, 1, st);

@@ -36,18 +36,28 @@ def negacyclic_sum_int64(keys, digits):
     return (out & 0xFFFFFFFF).astype(np.uint32)
 
 
-def _run_tc(keys, digits):
+def _run_tc(keys, digits, engine=0):
     import torch
     from paper_2205_05825_gb300 import binding as B
     out = torch.zeros((digits.shape[1], keys.shape[1]), dtype=torch.int32, device="cuda")
-    B.tc_negacyclic(to_dev(keys), to_dev(digits), out)
+    B.tc_negacyclic(to_dev(keys), to_dev(digits), out, engine=engine)
     return from_dev(out)
 
 
+def test_tc05_products_smallest_case(gpu_ready):
+    """The tcgen05 engine on its smallest launch (N = 256, 128 gates, one
+    key polynomial of random words): word for word."""
+    rng = np.random.default_rng(10)
+    keys = rng.integers(0, 2 ** 32, size=(1, 256), dtype=np.uint64).astype(np.uint32)
+    digits = rng.integers(-128, 128, size=(1, 128, 256)).astype(np.int8)
+    assert np.array_equal(_run_tc(keys, digits, engine=1), negacyclic_sum_int64(keys, digits))
+
+
+@pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("N", [256, 1024])
-def test_tc_products_adversarial_exact(gpu_ready, N):
+def test_tc_products_adversarial_exact(gpu_ready, N, engine):
     rng = np.random.default_rng(11)
-    G = 64
+    G = 64 if engine == 0 else 128
     cases = {
         "all -128 x -128": (np.full((1, N), 0x80808080, np.uint32), np.full((1, G, N), -128, np.int8)),
         "alternating": (np.tile(np.array([0x80808080, 0x7F7F7F7F], np.uint32), (3, N // 2)),
@@ -57,16 +67,18 @@ def test_tc_products_adversarial_exact(gpu_ready, N):
                    rng.integers(-128, 128, size=(3, G, N)).astype(np.int8)),
     }
     for name, (keys, digits) in cases.items():
-        assert np.array_equal(_run_tc(keys, digits), negacyclic_sum_int64(keys, digits)), name
+        assert np.array_equal(_run_tc(keys, digits, engine), negacyclic_sum_int64(keys, digits)), name
 
 
-def test_tc_products_several_gate_tiles(gpu_ready):
-    """192 gates (three CTA gate tiles), two chunks, random words."""
+@pytest.mark.parametrize("engine", [0, 1])
+def test_tc_products_several_gate_tiles(gpu_ready, engine):
+    """Three CTA gate tiles (192 gates for mma.sync, 384 for tcgen05), two
+    chunks, random words."""
     rng = np.random.default_rng(12)
-    N, G = 1024, 192
+    N, G = 1024, (192 if engine == 0 else 384)
     keys = rng.integers(0, 2 ** 32, size=(2, N), dtype=np.uint64).astype(np.uint32)
     digits = rng.integers(-128, 128, size=(2, G, N)).astype(np.int8)
-    assert np.array_equal(_run_tc(keys, digits), negacyclic_sum_int64(keys, digits))
+    assert np.array_equal(_run_tc(keys, digits, engine), negacyclic_sum_int64(keys, digits))
 
 
 def test_tc_products_rejects_bad_shapes(gpu_ready):
@@ -77,6 +89,10 @@ def test_tc_products_rejects_bad_shapes(gpu_ready):
     out = torch.zeros((65, 1024), dtype=torch.int32, device="cuda")
     with pytest.raises(B.MkError):
         B.tc_negacyclic(keys, digits, out)
+    d64 = torch.zeros((1, 64, 1024), dtype=torch.int8, device="cuda")
+    o64 = torch.zeros((64, 1024), dtype=torch.int32, device="cuda")
+    with pytest.raises(B.MkError):  # the tcgen05 engine takes whole 128-gate tiles
+        B.tc_negacyclic(keys, d64, o64, engine=1)
 
 
 @pytest.fixture(scope="module")
