@@ -140,6 +140,7 @@ struct TcArgs {
     const uint16_t *dig;
     size_t dig_zstride;
     int nchunks;
+    int dig_chunks;  // digit polynomials in the whole dig array (for the tcgen05 engine's tensor map)
 };
 // The tcgen05 engine of those products (mk_tensor_tc05.cu): G a multiple of
 // 128.  tc05_error reads (and optionally clears) the timeout record of its

@@ -361,6 +361,7 @@ cudaError_t blind_rotate_wave(const LaunchShape &S, const DeviceKeys &K, const T
         a.dig = reinterpret_cast<const uint16_t *>(w.U);
         a.dig_zstride = 3 * (size_t)Gp * N;
         a.nchunks = 3;
+        a.dig_chunks = 3 * (int)(k + 1);
         e = products<LOGN>(S.variant, a, Gp, 2 * (int)(k + 1), st);
         if (e != cudaSuccess) return e;
         tc_vdigits_kernel<LOGN><<<Gp, 256, 0, st>>>(k, Gp, S.bg_bit, w.V, w.Wd);
@@ -376,6 +377,7 @@ cudaError_t blind_rotate_wave(const LaunchShape &S, const DeviceKeys &K, const T
         b.dig = reinterpret_cast<const uint16_t *>(w.Wd);
         b.dig_zstride = 0;
         b.nchunks = 3;
+        b.dig_chunks = 3;
         e = products<LOGN>(S.variant, b, Gp, 2, st);
         if (e != cudaSuccess) return e;
         const int next = (step + 1 < steps) ? (int)(step + 1) : -1;
@@ -453,6 +455,7 @@ cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const
     a.key[0] = a.key[1] = keys;
     a.dig = reinterpret_cast<const uint16_t *>(d);
     a.nchunks = (int)nchunks;
+    a.dig_chunks = (int)nchunks;
     if (engine == 1) return launch_products_tc05(a, N, G, 1, st);
     cudaError_t e = N == 256 ? set_products_smem<8>() : set_products_smem<10>();
     if (e != cudaSuccess) return e;

@@ -18,14 +18,22 @@
 // starting at t0 + 8 (g' + kk): a K-major no-swizzle operand whose
 // leading- and stride-dimension byte offsets are both 128, read straight
 // from the unit array by the descriptor -- no per-tile copy of the matrix.
-// The digits (B operand, gates x coefficients) are staged per 64-coefficient
-// chunk with cp.async into core-matrix order, double buffered against the
-// MMAs.  The four planes accumulate in four 128-column TMEM blocks (all 512
-// columns); after each key polynomial every thread drains its own row
+// The digits (B operand, 128 gates x 64 coefficients per tile) arrive by TMA
+// (a 3-D tiled tensor map over [chunk][gate][coefficient], 128-byte swizzle)
+// into four stages: one thread of warp 1 produces tiles (expect-tx on the
+// stage's full barrier, wait on its empty barrier), one thread of warp 0
+// issues the MMAs (wait full, commit empty) -- no block-wide barrier inside
+// the K loop -- while warps 2 and 3 prepare the next key polynomial's byte
+// planes.  The four planes accumulate in four 128-column TMEM blocks (all
+// 512 columns); after each key polynomial every thread drains its own row
 // (tcgen05.ld 32x32b) into integer sums.  Every wait on an mbarrier is
 // bounded; on timeout the kernel records the fact and returns after
 // releasing TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "mk_internal.h"
 
@@ -51,16 +59,19 @@ template <int LOGN>
 struct T5Smem {
     static constexpr int N = 1 << LOGN;
     static constexpr int UNITS = N + 128;  // the K-steps read units [0, N + 120)
+    static constexpr int RLEN = UNITS + 8;  // R elements a plane's units cover (+ slack)
     static constexpr size_t plane_bytes = (size_t)UNITS * 16;
-    static constexpr size_t stage_bytes = (size_t)T5_NG * T5_KC * 2;
-    static constexpr size_t off_b = 4 * plane_bytes;
-    static constexpr size_t off_key = off_b + T5_STAGES * stage_bytes;
-    static constexpr size_t off_acc = off_key + (size_t)N * 4;  // integer sums [128 gates][128 rows]
-    static constexpr size_t off_bar = off_acc + (size_t)T5_NG * T5_M * 4;  // T5_STAGES mbarriers, then the TMEM address
-    static constexpr size_t used = off_bar + 8 * T5_STAGES + 16;
-    // More than half of the SM's shared memory: one CTA per SM, so the 512
-    // TMEM columns it allocates are always free.
-    static constexpr size_t bytes = used < 120 * 1024 ? 120 * 1024 : used;
+    static constexpr size_t stage_bytes = (size_t)T5_NG * T5_KC * 2;  // one TMA tile, 1024-byte aligned
+    // offsets from the 1024-byte aligned base
+    static constexpr size_t off_b = 0;
+    static constexpr size_t off_a = off_b + T5_STAGES * stage_bytes;
+    static constexpr size_t off_r = off_a + 4 * plane_bytes;              // [4 planes][2 copies][RLEN] bf16
+    static constexpr size_t off_acc = off_r + (size_t)4 * 2 * RLEN * 2;  // integer sums [128 gates][128 rows]
+    static constexpr size_t off_bar = off_acc + (size_t)T5_NG * T5_M * 4;  // full[S], empty[S], done; TMEM address
+    static constexpr size_t used = off_bar + 8 * (2 * T5_STAGES + 1) + 8;
+    // + 1 KB to align the base; more than half of the SM: one CTA per SM,
+    // so the 512 TMEM columns it allocates are always free
+    static constexpr size_t bytes = used + 1024 < 120 * 1024 ? 120 * 1024 : used + 1024;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,6 +81,26 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// K-major, 128-byte swizzle (TMA's CU_TENSOR_MAP_SWIZZLE_128B layout): rows
+// of 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -100,7 +131,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -109,35 +140,62 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
-}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
-// Grid (N / 128, G / 128, outputs), T5_THREADS threads.
+// The four byte planes of R_b[y] = ext_b[-y] for y = i - m0 - 127, i in
+// [0, RLEN), each in two copies one element apart (copy 1 holds element
+// i + 1 at i), so that any eight consecutive elements are four aligned
+// 32-bit words of one copy.  Threads [t0, t0 + nt) of the CTA take part.
 template <int LOGN>
-__global__ void __launch_bounds__(T5_THREADS, 1) tc05_products_kernel(TcArgs A, uint32_t G) {
+__device__ __forceinline__ void build_planes(const uint32_t *__restrict__ key, int m0, uint16_t *rpl, int t, int nt) {
+    using L = T5Smem<LOGN>;
+    constexpr int N = L::N;
+    for (int i = t; i < L::RLEN; i += nt) {
+        const int x = m0 + 127 - i;  // ext index
+        uint32_t v = 0;
+        bool neg = false;
+        if (x >= 0 && x < N) v = __ldg(key + x);
+        else if (x < 0 && x > -N) v = __ldg(key + x + N), neg = true;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int by = (int)(int8_t)(uint8_t)(v & 0xFFu);
+            v = (v - (uint32_t)by) >> 8;
+            const uint16_t hb = __bfloat16_as_ushort(__int2bfloat16_rn(neg ? -by : by));
+            rpl[(2 * b) * L::RLEN + i] = hb;
+            if (i > 0) rpl[(2 * b + 1) * L::RLEN + i - 1] = hb;
+        }
+    }
+}
+
+// Grid (N / 128, G / 128, outputs), T5_THREADS threads; dmap: the digits
+// as a [chunks][G][N] bf16 tensor, tile box 64 x 128 x 1, 128-byte swizzle.
+template <int LOGN>
+__global__ void __launch_bounds__(T5_THREADS, 1)
+    tc05_products_kernel(TcArgs A, uint32_t G, const __grid_constant__ CUtensorMap dmap) {
     using L = T5Smem<LOGN>;
     constexpr int N = L::N, UNITS = L::UNITS;
-    constexpr int KSTEPS = N / T5_KC;  // staged digit tiles per key polynomial
-    extern __shared__ __align__(1024) unsigned char smem[];
-    uint32_t *skey = reinterpret_cast<uint32_t *>(smem + L::off_key);
+    constexpr int KSTEPS = N / T5_KC;  // digit tiles per key polynomial
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
+    uint16_t *rpl = reinterpret_cast<uint16_t *>(smem + L::off_r);      // plane b, copy c at (2 b + c) * RLEN
     uint32_t *sacc = reinterpret_cast<uint32_t *>(smem + L::off_acc);  // [gate][row]: row = tid, conflict-free
-    const uint32_t bar0 = smem_addr(smem + L::off_bar);  // barrier of stage s at bar0 + 8 s
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::off_bar + 8 * T5_STAGES);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t full0 = smem_addr(smem + L::off_bar);                // full[s] = full0 + 8 s
+    const uint32_t empty0 = full0 + 8 * T5_STAGES;                      // empty[s] = empty0 + 8 s
+    const uint32_t done = empty0 + 8 * T5_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::off_bar + 8 * (2 * T5_STAGES + 1));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int type = blockIdx.z & 1, zi = blockIdx.z >> 1;
     const int m0 = blockIdx.x * T5_M;
     const uint32_t g0 = blockIdx.y * T5_NG;
     const uint32_t *keyz = type ? A.key[1] + zi * A.key_zstride[1] : A.key[0] + zi * A.key_zstride[0];
-    const uint16_t *digz = A.dig + zi * A.dig_zstride + (size_t)g0 * N;
-    const uint32_t a_base = smem_addr(smem), b_base = smem_addr(smem + L::off_b);
+    const int chunk0 = (int)(zi * (A.dig_zstride / ((size_t)G * N)));  // first digit polynomial of this output
+    const uint32_t a_base = smem_addr(smem + L::off_a), b_base = smem_addr(smem + L::off_b);
 
     if (tid == 0) {
-        for (int q = 0; q < T5_STAGES; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8 * q) : "memory");
+        for (int q = 0; q < 2 * T5_STAGES + 1; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -146,123 +204,111 @@ __global__ void __launch_bounds__(T5_THREADS, 1) tc05_products_kernel(TcArgs A, 
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    for (int g = 0; g < T5_NG; ++g) sacc[g * T5_M + tid] = 0;
+    build_planes<LOGN>(keyz, m0, rpl, tid, T5_THREADS);  // key polynomial 0
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-
-    for (int g = 0; g < T5_NG; ++g) sacc[g * T5_M + tid] = 0;
     bool ok = true;
-    // Tile j (over all key polynomials) uses stage j % T5_STAGES; its MMAs
-    // commit to that stage's barrier as the stage's (j / T5_STAGES)-th use.
-    uint32_t j = 0;
-    auto stage_bar = [&](uint32_t t) { return bar0 + 8 * (t % T5_STAGES); };
-    auto wait_tile = [&](uint32_t t) { return mbar_wait(stage_bar(t), (t / T5_STAGES) & 1); };
-    // digits of 128 gates x 64 coefficients into core-matrix order: core
-    // (gate group ng, column group kg) at (ng * 8 + kg) * 128, row r at + r * 16
-    auto load_tile = [&](const uint16_t *dig, int kc, uint32_t t) {
-        const uint32_t sb = b_base + (t % T5_STAGES) * (uint32_t)L::stage_bytes;
-        for (int q = tid; q < T5_NG * (T5_KC / 8); q += T5_THREADS) {
-            const int gate = q >> 3, kg = q & 7;
-            const uint32_t dst = sb + (uint32_t)(((gate >> 3) * 8 + kg) * 128 + (gate & 7) * 16);
-            cp_async16(dst, dig + (size_t)gate * N + kc * T5_KC + kg * 8);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
 
-    for (int c = 0; c < A.nchunks && ok; ++c) {
-        const uint32_t *key = keyz + (size_t)c * N;
-        const uint16_t *dig = digz + (size_t)c * G * N;
-        const uint32_t j0 = j;  // first tile of this key polynomial
-        // start the first two digit tiles (their stages are free: every MMA
-        // of the previous key polynomial has completed)
-        load_tile(dig, 0, j0);
-        load_tile(dig, 1, j0 + 1);
-        // key words, then the four unit arrays: unit ui holds R_b[ui - m0 - 127 + e],
-        // e = 0..7, with R_b[y] = ext_b[-y]
-        for (int x = tid; x < N; x += T5_THREADS) skey[x] = key[x];
-        __syncthreads();
+    for (int c = 0; c < A.nchunks; ++c) {
+        // unit ui = R elements [ui, ui + 8) of each plane
         for (int ui = tid; ui < UNITS; ui += T5_THREADS) {
-            uint32_t packed[4][4];
+            const int cp = ui & 1;
+            const int w0 = (ui - cp) >> 1;  // first word of the window in copy cp
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int x = m0 + 127 - ui - e;  // ext index
-                uint32_t v = 0;
-                bool neg = false;
-                if (x >= 0 && x < N) v = skey[x];
-                else if (x < 0 && x > -N) v = skey[x + N], neg = true;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int by = (int)(int8_t)(uint8_t)(v & 0xFFu);
-                    v = (v - (uint32_t)by) >> 8;
-                    const __nv_bfloat16 h = __int2bfloat16_rn(neg ? -by : by);
-                    const uint32_t hb = (uint32_t)__bfloat16_as_ushort(h);
-                    if (e & 1) packed[b][e >> 1] |= hb << 16;
-                    else packed[b][e >> 1] = hb;
-                }
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(rpl + (2 * b + cp) * L::RLEN) + w0;
+                *reinterpret_cast<uint4 *>(smem + L::off_a + (size_t)b * L::plane_bytes + (size_t)ui * 16) =
+                    make_uint4(wp[0], wp[1], wp[2], wp[3]);
             }
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                *reinterpret_cast<uint4 *>(smem + (size_t)b * L::plane_bytes + (size_t)ui * 16) =
-                    make_uint4(packed[b][0], packed[b][1], packed[b][2], packed[b][3]);
         }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
 
-        for (int kc = 0; kc < KSTEPS; ++kc, ++j) {
-            // tile j + 2 goes into the stage tile j - 2 used: its MMAs must be
-            // done (for kc < 2 that stage held a tile of the previous key
-            // polynomial, whose MMAs all completed before its drain)
-            if (kc + 2 < KSTEPS) {
-                if (kc >= 2 && !wait_tile(j - 2)) ok = false;
-                if (__syncthreads_and(ok) == 0) {
+        // Roles for the K loop: whole warps follow their loop in step (lane 0
+        // issues), so no lane spins beside the one issuing.
+        if (warp == 1) {
+            // producer: tile j = c * KSTEPS + kc into stage j % S once the
+            // MMAs of tile j - S (same stage) have committed
+            for (int kc = 0; kc < KSTEPS; ++kc) {
+                const uint32_t j = (uint32_t)(c * KSTEPS + kc), st = j % T5_STAGES;
+                if (j >= T5_STAGES && !mbar_wait(empty0 + 8 * st, ((j / T5_STAGES) - 1) & 1)) ok = false;
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
                     break;
                 }
-                load_tile(dig, kc + 2, j + 2);
-                asm volatile("cp.async.wait_group 2;\n" ::: "memory");  // tile j has landed
-            } else if (kc + 1 < KSTEPS) {
-                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-            } else {
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t sb = b_base + (j % T5_STAGES) * (uint32_t)L::stage_bytes;
-#pragma unroll
-                for (int s = 0; s < T5_KC / 16; ++s) {
-                    const int t0 = kc * T5_KC + s * 16;
-                    const uint64_t bdesc = smem_desc(sb + (uint32_t)(2 * s * 128), 128, 8 * 128);
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const uint64_t adesc = smem_desc(a_base + (uint32_t)(b * L::plane_bytes + t0 * 16), 128, 128);
-                        mma_issue(tmem + (uint32_t)(b * T5_NG), adesc, bdesc, (kc | s) ? 1u : 0u);
-                    }
+                if (lane == 0) {
+                    mbar_expect_tx(full0 + 8 * st, (uint32_t)L::stage_bytes);
+                    tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)g0, chunk0 + c,
+                                full0 + 8 * st);
                 }
-                mma_commit(stage_bar(j));
+                __syncwarp();
             }
+        } else if (warp == 0) {
+            // MMA issuer; afterwards this warp alone waits for the commit of
+            // every MMA of the key polynomial, the others wait at the barrier
+            const uint64_t adesc0 = smem_desc(a_base, 128, 128);
+            for (int kc = 0; kc < KSTEPS; ++kc) {
+                const uint32_t j = (uint32_t)(c * KSTEPS + kc), st = j % T5_STAGES;
+                if (!mbar_wait(full0 + 8 * st, (j / T5_STAGES) & 1)) ok = false;
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint64_t bdesc0 = smem_desc_sw128(b_base + st * (uint32_t)L::stage_bytes);
+#pragma unroll
+                    for (int s4 = 0; s4 < T5_KC / 16; ++s4) {
+                        const int t0 = kc * T5_KC + s4 * 16;
+                        const uint64_t bdesc = bdesc0 + (uint64_t)(s4 * 32 / 16);  // 32 bytes per K-step of 16
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const uint64_t adesc = adesc0 + (uint64_t)((b * L::plane_bytes + t0 * 16) / 16);
+                            mma_issue(tmem + (uint32_t)(b * T5_NG), adesc, bdesc, (kc | s4) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(empty0 + 8 * st);
+                }
+                __syncwarp();
+            }
+            if (ok) {
+                if (lane == 0) mma_commit(done);  // every MMA of this key polynomial
+                __syncwarp();
+                if (!mbar_wait(done, c & 1)) ok = false;
+            }
+        } else if (c + 1 < A.nchunks) {
+            // warps 2 and 3: the next key polynomial's planes (the units above
+            // were built from the current ones)
+            build_planes<LOGN>(keyz + (size_t)(c + 1) * N, m0, rpl, tid - 64, 64);
         }
-        if (!ok) break;
-        // the last two tiles' MMAs were not waited for above; the last commit
-        // covers every earlier MMA of the key polynomial
-        if (!wait_tile(j - 2) || !wait_tile(j - 1)) ok = false;
         if (__syncthreads_and(ok) == 0) {
             ok = false;
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll 1
+        for (int q = 0; q < T5_NG / 32; ++q) {  // gates 32 q .. 32 q + 31, all four planes
+            uint32_t r0[32], r1[32], r2[32], r3[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32);
+            tmem_ld32_nowait(ta, r0);
+            tmem_ld32_nowait(ta + T5_NG, r1);
+            tmem_ld32_nowait(ta + 2 * T5_NG, r2);
+            tmem_ld32_nowait(ta + 3 * T5_NG, r3);
+            tmem_wait_ld();
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int q = 0; q < T5_NG / 32; ++q) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * T5_NG + q * 32), r);
-#pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    sacc[(q * 32 + i) * T5_M + tid] += (uint32_t)__float2int_rn(__uint_as_float(r[i])) << (8 * b);
+            for (int i = 0; i < 32; ++i) {
+                const uint32_t v = (uint32_t)__float2int_rn(__uint_as_float(r0[i])) +
+                                   ((uint32_t)__float2int_rn(__uint_as_float(r1[i])) << 8) +
+                                   ((uint32_t)__float2int_rn(__uint_as_float(r2[i])) << 16) +
+                                   ((uint32_t)__float2int_rn(__uint_as_float(r3[i])) << 24);
+                sacc[(q * 32 + i) * T5_M + tid] += v;
             }
+        }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();  // TMEM drained and units read: the next key polynomial may overwrite both
+        __syncthreads();  // TMEM drained, units read, next planes built
     }
 
     if (ok) {
@@ -274,13 +320,11 @@ __global__ void __launch_bounds__(T5_THREADS, 1) tc05_products_kernel(TcArgs A, 
             const uint32_t v = sacc[g * T5_M + tid];
             *d = A.accumulate ? (int32_t)((uint32_t)*d + v) : (int32_t)v;
         }
-    } else {
-        asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy may land after the CTA exits
-        if (tid == 0) {
-            atomicCAS(&g_tc05_error, 0u, 1u + blockIdx.x + 1024u * blockIdx.y);
-            // let MMAs still in flight finish before their TMEM goes away (bounded)
-            mbar_wait(bar0, 0);
-        }
+    } else if (tid == 0) {
+        atomicCAS(&g_tc05_error, 0u, 1u + blockIdx.x + 1024u * blockIdx.y);
+        // let copies and MMAs still in flight land before their memory goes away (bounded)
+        for (int q = 0; q < T5_STAGES; ++q) mbar_wait(full0 + 8 * q, 0);
+        mbar_wait(done, 0);
     }
     __syncthreads();
     if (warp == 0)
@@ -290,14 +334,43 @@ __global__ void __launch_bounds__(T5_THREADS, 1) tc05_products_kernel(TcArgs A, 
 
 }  // namespace
 
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+}  // namespace
+
 template <int LOGN>
 static cudaError_t launch_tc05(const TcArgs &A, uint32_t G, int outputs, cudaStream_t st) {
     constexpr int N = 1 << LOGN;
-    if (G % T5_NG) return cudaErrorInvalidValue;
+    if (G % T5_NG || A.dig_chunks <= 0) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // digits: [dig_chunks][G][N] bf16; a box of 64 coefficients x 128 gates x 1 polynomial
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)G, (cuuint64_t)A.dig_chunks};
+    const cuuint64_t strides[2] = {(cuuint64_t)N * 2, (cuuint64_t)G * N * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)T5_KC, (cuuint32_t)T5_NG, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t *>(A.dig), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tc05_products_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)T5Smem<LOGN>::bytes);
     if (e != cudaSuccess) return e;
-    tc05_products_kernel<LOGN><<<dim3(N / T5_M, G / T5_NG, outputs), T5_THREADS, T5Smem<LOGN>::bytes, st>>>(A, G);
+    tc05_products_kernel<LOGN><<<dim3(N / T5_M, G / T5_NG, outputs), T5_THREADS, T5Smem<LOGN>::bytes, st>>>(A, G,
+                                                                                                           map);
     return cudaGetLastError();
 }
 
