@@ -248,28 +248,37 @@ struct Ntt {
     static constexpr int PN = N + N / 16;  // padded polynomial stride in xbuf
 
     // Forward stage at bit b (distance 2^b) inside a pass with element bits
-    // [LO, LO+SB): element pairs (c, c + D), D = 2^(b - LO).
+    // [LO, LO+SB): element pairs (c, c + D), D = 2^(b - LO).  The pair's
+    // twiddle index m + ((jb | c << LO) >> (b + 1)) splits into a per-stage
+    // base m + (jb >> (b + 1)) plus c / (2 D) (jb has no bits in [LO, LO+SB)),
+    // so a stage needs only EPT / (2 D) distinct twiddles.
     template <int NP, int D>
     __device__ static __forceinline__ void fwd_stage(E (&x)[NP][EPT], int jb, int LO, int b, const Tw *tw) {
-        const int m = 1 << (LOGN - 1 - b);
+        constexpr int NT = EPT / (2 * D), SH = (D == 4 ? 3 : (D == 2 ? 2 : 1));  // 2 D = 2^SH
+        const int base = (1 << (LOGN - 1 - b)) + (jb >> (b + 1));
+        Tw S[NT];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) S[q] = twiddle(tw, base + q);
 #pragma unroll
         for (int c = 0; c < EPT; ++c) {
             if (c & D) continue;
-            const Tw S = twiddle(tw, m + ((jb | (c << LO)) >> (b + 1)));
 #pragma unroll
-            for (int p = 0; p < NP; ++p) F::fwd(x[p][c], x[p][c + D], S);
+            for (int p = 0; p < NP; ++p) F::fwd(x[p][c], x[p][c + D], S[c >> SH]);
         }
     }
 
     template <int NP, int D>
     __device__ static __forceinline__ void inv_stage(E (&x)[NP][EPT], int jb, int LO, int b, const Tw *tw) {
-        const int m = 1 << (LOGN - 1 - b);
+        constexpr int NT = EPT / (2 * D), SH = (D == 4 ? 3 : (D == 2 ? 2 : 1));  // 2 D = 2^SH
+        const int base = (1 << (LOGN - 1 - b)) + (jb >> (b + 1));
+        Tw S[NT];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) S[q] = twiddle(tw, base + q);
 #pragma unroll
         for (int c = 0; c < EPT; ++c) {
             if (c & D) continue;
-            const Tw S = twiddle(tw, m + ((jb | (c << LO)) >> (b + 1)));
 #pragma unroll
-            for (int p = 0; p < NP; ++p) F::inv(x[p][c], x[p][c + D], S);
+            for (int p = 0; p < NP; ++p) F::inv(x[p][c], x[p][c + D], S[c >> SH]);
         }
     }
 
