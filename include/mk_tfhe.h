@@ -163,7 +163,9 @@ int mk_autotune_form(mk_ctx *ctx, uint32_t sample_gates, uint32_t forms, int *be
 const char *mk_last_error(const mk_ctx *ctx);
 
 /* Wait for all work enqueued on the context's stream; reports any
- * asynchronous CUDA error as MK_EDEVICE. */
+ * asynchronous CUDA error as MK_EDEVICE, and MK_ETIMEOUT if a bounded
+ * device-side wait of the tensor form's tcgen05 engine gave up since the
+ * last check (its results are then invalid). */
 int mk_sync(mk_ctx *ctx);
 
 /* ---------------------------------------------------------------- keys */

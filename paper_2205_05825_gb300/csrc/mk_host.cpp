@@ -772,6 +772,11 @@ int mk_sync(mk_ctx *c) {
     MK_CUDA(c, cudaSetDevice(c->device));
     MK_CUDA(c, cudaStreamSynchronize(c->stream));
     MK_CUDA(c, cudaGetLastError());
+    if (c->form == MK_FORM_TC && c->dev_keys_valid) {  // the tcgen05 engine's bounded waits
+        unsigned int timeout = 0;
+        MK_CUDA(c, tc05_error(&timeout, true));
+        if (timeout) return fail(c, MK_ETIMEOUT, "a bounded wait of the tensor-core product kernel gave up");
+    }
     return MK_OK;
 }
 
