@@ -20,15 +20,16 @@
 // from the unit array by the descriptor -- no per-tile copy of the matrix.
 // The digits (B operand, 128 gates x 64 coefficients per tile) arrive by TMA
 // (a 3-D tiled tensor map over [chunk][gate][coefficient], 128-byte swizzle)
-// into four stages: one thread of warp 1 produces tiles (expect-tx on the
-// stage's full barrier, wait on its empty barrier), one thread of warp 0
-// issues the MMAs (wait full, commit empty) -- no block-wide barrier inside
-// the K loop -- while warps 2 and 3 prepare the next key polynomial's byte
-// planes.  The four planes accumulate in four 128-column TMEM blocks (all
-// 512 columns); after each key polynomial every thread drains its own row
-// (tcgen05.ld 32x32b) into integer sums.  Every wait on an mbarrier is
-// bounded; on timeout the kernel records the fact and returns after
-// releasing TMEM.
+// into four stages: warp 5 produces tiles (expect-tx on the stage's full
+// barrier, wait on its empty barrier), warp 4 issues the MMAs (wait full,
+// commit empty) -- no block-wide barrier inside the K loop.  Each key
+// polynomial is two passes over K, one per pair of byte planes, into the two
+// 256-column halves of TMEM (plane b in columns 128 b .. 128 b + 127): while
+// the MMAs of one pass run, warps 0-3 drain the other half (tcgen05.ld
+// 32x32b, one row per thread, into integer sums) and build the unit arrays
+// of the pass after, then signal it through that half's ready barrier.
+// Every wait on an mbarrier is bounded; on timeout the kernel records the
+// fact and returns after releasing TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -44,7 +45,8 @@ constexpr int T5_M = 128;       // output coefficients per CTA (TMEM lanes)
 constexpr int T5_NG = 128;      // gates per CTA (MMA N)
 constexpr int T5_KC = 64;       // coefficients per staged digit tile
 constexpr int T5_STAGES = 4;    // digit tiles in flight: loads run two tiles ahead of the MMAs
-constexpr int T5_THREADS = 128;
+constexpr int T5_WORKERS = 128;               // warps 0-3: TMEM drain (one row each), unit arrays, planes
+constexpr int T5_THREADS = T5_WORKERS + 64;   // + warp 4 (MMA issue) + warp 5 (TMA producer)
 constexpr uint32_t T5_TMEM_COLS = 512;
 constexpr uint32_t T5_WAIT_LIMIT = 1u << 26;
 
@@ -67,8 +69,9 @@ struct T5Smem {
     static constexpr size_t off_a = off_b + T5_STAGES * stage_bytes;
     static constexpr size_t off_r = off_a + 4 * plane_bytes;              // [4 planes][2 copies][RLEN] bf16
     static constexpr size_t off_acc = off_r + (size_t)4 * 2 * RLEN * 2;  // integer sums [128 gates][128 rows]
-    static constexpr size_t off_bar = off_acc + (size_t)T5_NG * T5_M * 4;  // full[S], empty[S], done; TMEM address
-    static constexpr size_t used = off_bar + 8 * (2 * T5_STAGES + 1) + 8;
+    static constexpr size_t off_bar = off_acc + (size_t)T5_NG * T5_M * 4;  // mbarriers, then the TMEM address
+    static constexpr int NBARS = 2 * T5_STAGES + 4;  // full[S], empty[S], done[2], ready[2]
+    static constexpr size_t used = off_bar + 8 * NBARS + 8;
     // + 1 KB to align the base; more than half of the SM: one CTA per SM,
     // so the 512 TMEM columns it allocates are always free
     static constexpr size_t bytes = used + 1024 < 120 * 1024 ? 120 * 1024 : used + 1024;
@@ -169,33 +172,72 @@ __device__ __forceinline__ void build_planes(const uint32_t *__restrict__ key, i
     }
 }
 
+// Unit ui of plane b = R_b elements [ui, ui + 8), for planes b0 and b0 + 1,
+// by the worker threads.
+template <int LOGN>
+__device__ __forceinline__ void build_units(unsigned char *a, const uint16_t *rpl, int b0, int t) {
+    using L = T5Smem<LOGN>;
+    for (int ui = t; ui < L::UNITS; ui += T5_WORKERS) {
+        const int cp = ui & 1;
+        const int w0 = (ui - cp) >> 1;  // first word of the window in copy cp
+#pragma unroll
+        for (int b = b0; b < b0 + 2; ++b) {
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(rpl + (2 * b + cp) * L::RLEN) + w0;
+            *reinterpret_cast<uint4 *>(a + (size_t)b * L::plane_bytes + (size_t)ui * 16) =
+                make_uint4(wp[0], wp[1], wp[2], wp[3]);
+        }
+    }
+}
+
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(T5_WORKERS) : "memory"); }
+
+// Barrier of the worker warps that also ANDs their flags, so that all of them
+// take the same branch after a bounded wait.
+__device__ __forceinline__ bool workers_all(bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "n"(T5_WORKERS)
+        : "memory");
+    return r != 0;
+}
+
 // Grid (N / 128, G / 128, outputs), T5_THREADS threads; dmap: the digits
 // as a [chunks][G][N] bf16 tensor, tile box 64 x 128 x 1, 128-byte swizzle.
 template <int LOGN>
 __global__ void __launch_bounds__(T5_THREADS, 1)
     tc05_products_kernel(TcArgs A, uint32_t G, const __grid_constant__ CUtensorMap dmap) {
     using L = T5Smem<LOGN>;
-    constexpr int N = L::N, UNITS = L::UNITS;
+    constexpr int N = L::N;
     constexpr int KSTEPS = N / T5_KC;  // digit tiles per key polynomial
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
     uint16_t *rpl = reinterpret_cast<uint16_t *>(smem + L::off_r);      // plane b, copy c at (2 b + c) * RLEN
     uint32_t *sacc = reinterpret_cast<uint32_t *>(smem + L::off_acc);  // [gate][row]: row = tid, conflict-free
-    const uint32_t full0 = smem_addr(smem + L::off_bar);                // full[s] = full0 + 8 s
-    const uint32_t empty0 = full0 + 8 * T5_STAGES;                      // empty[s] = empty0 + 8 s
-    const uint32_t done = empty0 + 8 * T5_STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::off_bar + 8 * (2 * T5_STAGES + 1));
+    const uint32_t full0 = smem_addr(smem + L::off_bar);  // full[s] = full0 + 8 s
+    const uint32_t empty0 = full0 + 8 * T5_STAGES;        // empty[s] = empty0 + 8 s
+    const uint32_t done0 = empty0 + 8 * T5_STAGES;        // done[h]: every MMA of a pass on half h
+    const uint32_t ready0 = done0 + 16;                   // ready[h]: half h drained, its next units built
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::off_bar + 8 * L::NBARS);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int type = blockIdx.z & 1, zi = blockIdx.z >> 1;
     const int m0 = blockIdx.x * T5_M;
     const uint32_t g0 = blockIdx.y * T5_NG;
     const uint32_t *keyz = type ? A.key[1] + zi * A.key_zstride[1] : A.key[0] + zi * A.key_zstride[0];
     const int chunk0 = (int)(zi * (A.dig_zstride / ((size_t)G * N)));  // first digit polynomial of this output
-    const uint32_t a_base = smem_addr(smem + L::off_a), b_base = smem_addr(smem + L::off_b);
+    unsigned char *abuf = smem + L::off_a;
+    const uint32_t a_base = smem_addr(abuf), b_base = smem_addr(smem + L::off_b);
+    const int P = 2 * A.nchunks;  // passes p = 2 c + h: key polynomial c, planes 2h and 2h + 1
 
     if (tid == 0) {
-        for (int q = 0; q < 2 * T5_STAGES + 1; ++q)
+        for (int q = 0; q < 2 * T5_STAGES + 2; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * q) : "memory");
+        for (int h = 0; h < 2; ++h)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ready0 + 8 * h), "n"(T5_WORKERS) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -204,36 +246,26 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    for (int g = 0; g < T5_NG; ++g) sacc[g * T5_M + tid] = 0;
-    build_planes<LOGN>(keyz, m0, rpl, tid, T5_THREADS);  // key polynomial 0
+    if (warp < 4) {  // passes 0 and 1: key polynomial 0, all four planes
+        for (int g = 0; g < T5_NG; ++g) sacc[g * T5_M + tid] = 0;
+        build_planes<LOGN>(keyz, m0, rpl, tid, T5_WORKERS);
+        workers_sync();
+        build_units<LOGN>(abuf, rpl, 0, tid);
+        build_units<LOGN>(abuf, rpl, 2, tid);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
-    for (int c = 0; c < A.nchunks; ++c) {
-        // unit ui = R elements [ui, ui + 8) of each plane
-        for (int ui = tid; ui < UNITS; ui += T5_THREADS) {
-            const int cp = ui & 1;
-            const int w0 = (ui - cp) >> 1;  // first word of the window in copy cp
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(rpl + (2 * b + cp) * L::RLEN) + w0;
-                *reinterpret_cast<uint4 *>(smem + L::off_a + (size_t)b * L::plane_bytes + (size_t)ui * 16) =
-                    make_uint4(wp[0], wp[1], wp[2], wp[3]);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-
-        // Roles for the K loop: whole warps follow their loop in step (lane 0
-        // issues), so no lane spins beside the one issuing.
-        if (warp == 1) {
-            // producer: tile j = c * KSTEPS + kc into stage j % S once the
-            // MMAs of tile j - S (same stage) have committed
+    if (warp == 5) {
+        // producer: tile j = p * KSTEPS + kc into stage j % S once the MMAs
+        // of tile j - S (same stage) have committed
+        for (int p = 0; p < P && ok; ++p)
             for (int kc = 0; kc < KSTEPS; ++kc) {
-                const uint32_t j = (uint32_t)(c * KSTEPS + kc), st = j % T5_STAGES;
+                const uint32_t j = (uint32_t)(p * KSTEPS + kc), st = j % T5_STAGES;
                 if (j >= T5_STAGES && !mbar_wait(empty0 + 8 * st, ((j / T5_STAGES) - 1) & 1)) ok = false;
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
@@ -241,17 +273,25 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                 }
                 if (lane == 0) {
                     mbar_expect_tx(full0 + 8 * st, (uint32_t)L::stage_bytes);
-                    tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)g0, chunk0 + c,
-                                full0 + 8 * st);
+                    tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)g0,
+                                chunk0 + (p >> 1), full0 + 8 * st);
                 }
                 __syncwarp();
             }
-        } else if (warp == 0) {
-            // MMA issuer; afterwards this warp alone waits for the commit of
-            // every MMA of the key polynomial, the others wait at the barrier
-            const uint64_t adesc0 = smem_desc(a_base, 128, 128);
+    } else if (warp == 4) {
+        // MMA issuer
+        const uint64_t adesc0 = smem_desc(a_base, 128, 128);
+        for (int p = 0; p < P && ok; ++p) {
+            const int h = p & 1;
+            // passes 0 and 1 were prepared before the roles split; later ones
+            // wait until their TMEM half is drained and their units are built
+            if (p >= 2 && !mbar_wait(ready0 + 8 * h, ((p >> 1) - 1) & 1)) ok = false;
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                ok = false;
+                break;
+            }
             for (int kc = 0; kc < KSTEPS; ++kc) {
-                const uint32_t j = (uint32_t)(c * KSTEPS + kc), st = j % T5_STAGES;
+                const uint32_t j = (uint32_t)(p * KSTEPS + kc), st = j % T5_STAGES;
                 if (!mbar_wait(full0 + 8 * st, (j / T5_STAGES) & 1)) ok = false;
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
@@ -265,7 +305,8 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                         const int t0 = kc * T5_KC + s4 * 16;
                         const uint64_t bdesc = bdesc0 + (uint64_t)(s4 * 32 / 16);  // 32 bytes per K-step of 16
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
+                        for (int bb = 0; bb < 2; ++bb) {
+                            const int b = 2 * h + bb;
                             const uint64_t adesc = adesc0 + (uint64_t)((b * L::plane_bytes + t0 * 16) / 16);
                             mma_issue(tmem + (uint32_t)(b * T5_NG), adesc, bdesc, (kc | s4) ? 1u : 0u);
                         }
@@ -274,57 +315,66 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                 }
                 __syncwarp();
             }
-            if (ok) {
-                if (lane == 0) mma_commit(done);  // every MMA of this key polynomial
-                __syncwarp();
-                if (!mbar_wait(done, c & 1)) ok = false;
-            }
-        } else if (c + 1 < A.nchunks) {
-            // warps 2 and 3: the next key polynomial's planes (the units above
-            // were built from the current ones)
-            build_planes<LOGN>(keyz + (size_t)(c + 1) * N, m0, rpl, tid - 64, 64);
+            if (!ok) break;
+            if (lane == 0) mma_commit(done0 + 8 * h);  // every MMA of pass p
+            __syncwarp();
         }
-        if (__syncthreads_and(ok) == 0) {
-            ok = false;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    } else {
+        // workers, step p: once pass p - 1 has completed, drain its half;
+        // then build the units of pass p + 1 (same half: its previous MMAs
+        // were pass p - 1) and release it.  The planes of key polynomial
+        // c + 1 are built once both halves of polynomial c have their units.
+        for (int p = 0; p <= P; ++p) {
+            if (p >= 1) {
+                const int hp = (p - 1) & 1;
+                ok = workers_all(mbar_wait(done0 + 8 * hp, ((p - 1) >> 1) & 1));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
-        for (int q = 0; q < T5_NG / 32; ++q) {  // gates 32 q .. 32 q + 31, all four planes
-            uint32_t r0[32], r1[32], r2[32], r3[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32);
-            tmem_ld32_nowait(ta, r0);
-            tmem_ld32_nowait(ta + T5_NG, r1);
-            tmem_ld32_nowait(ta + 2 * T5_NG, r2);
-            tmem_ld32_nowait(ta + 3 * T5_NG, r3);
-            tmem_wait_ld();
+                for (int q = 0; q < T5_NG / 32; ++q) {  // gates 32 q .. 32 q + 31, planes 2 hp and 2 hp + 1
+                    uint32_t r0[32], r1[32];
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(2 * hp * T5_NG + q * 32);
+                    tmem_ld32_nowait(ta, r0);
+                    tmem_ld32_nowait(ta + T5_NG, r1);
+                    tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const uint32_t v = (uint32_t)__float2int_rn(__uint_as_float(r0[i])) +
-                                   ((uint32_t)__float2int_rn(__uint_as_float(r1[i])) << 8) +
-                                   ((uint32_t)__float2int_rn(__uint_as_float(r2[i])) << 16) +
-                                   ((uint32_t)__float2int_rn(__uint_as_float(r3[i])) << 24);
-                sacc[(q * 32 + i) * T5_M + tid] += v;
+                    for (int i = 0; i < 32; ++i) {
+                        const uint32_t v = (uint32_t)__float2int_rn(__uint_as_float(r0[i])) +
+                                           ((uint32_t)__float2int_rn(__uint_as_float(r1[i])) << 8);
+                        sacc[(q * 32 + i) * T5_M + tid] += v << (16 * hp);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            }
+            const int q = p + 1, cq = q >> 1, hq = q & 1;
+            if (q >= 2 && q < P) {
+                workers_sync();  // the planes of key polynomial cq are complete
+                build_units<LOGN>(abuf, rpl, 2 * hq, tid);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(ready0 + 8 * hq) : "memory");
+            }
+            if (hq == 1 && cq + 1 < A.nchunks) {
+                workers_sync();  // every unit of key polynomial cq is built: the planes may be replaced
+                build_planes<LOGN>(keyz + (size_t)(cq + 1) * N, m0, rpl, tid, T5_WORKERS);
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();  // TMEM drained, units read, next planes built
     }
-
-    if (ok) {
-        // row r' = tid holds coefficient m0 + 127 - tid of every gate
-        int32_t *dst = (type ? A.dst[1] : A.dst[0]) + zi * A.dst_zstride;
-        const int m = m0 + 127 - tid;
-        for (int g = 0; g < T5_NG; ++g) {
-            int32_t *d = dst + (size_t)(g0 + g) * A.dst_stride + m;
-            const uint32_t v = sacc[g * T5_M + tid];
-            *d = A.accumulate ? (int32_t)((uint32_t)*d + v) : (int32_t)v;
+    if (__syncthreads_and(ok)) {
+        if (warp < 4) {
+            // row r' = tid holds coefficient m0 + 127 - tid of every gate
+            int32_t *dst = (type ? A.dst[1] : A.dst[0]) + zi * A.dst_zstride;
+            const int m = m0 + 127 - tid;
+            for (int g = 0; g < T5_NG; ++g) {
+                int32_t *d = dst + (size_t)(g0 + g) * A.dst_stride + m;
+                const uint32_t v = sacc[g * T5_M + tid];
+                *d = A.accumulate ? (int32_t)((uint32_t)*d + v) : (int32_t)v;
+            }
         }
     } else if (tid == 0) {
         atomicCAS(&g_tc05_error, 0u, 1u + blockIdx.x + 1024u * blockIdx.y);
         // let copies and MMAs still in flight land before their memory goes away (bounded)
         for (int q = 0; q < T5_STAGES; ++q) mbar_wait(full0 + 8 * q, 0);
-        mbar_wait(done, 0);
+        mbar_wait(done0, 0);
     }
     __syncthreads();
     if (warp == 0)
