@@ -8,7 +8,8 @@
 // with bf16 operands (signed bytes and 8-bit digits are exact in bf16) and
 // fp32 accumulation, exact while every (chunk, plane) sum stays within 2^24.
 //
-// A CTA owns 128 output coefficients m0..m0+127 and 128 gates.  The MMA's row
+// A work item is 128 output coefficients m0..m0+127 of 128 gates; one
+// persistent CTA per SM loops over items.  The MMA's row
 // r' stands for coefficient m = m0 + 127 - r' (rows reversed), so element
 // (r', t) of the A operand is R[t - m0 - 127 + r'] with R[y] = ext[-y]: a
 // Hankel matrix, constant along anti-diagonals.  Shared memory holds, per
@@ -70,7 +71,7 @@ struct T5Smem {
     static constexpr size_t off_r = off_a + 4 * plane_bytes;              // [4 planes][2 copies][RLEN] bf16
     static constexpr size_t off_acc = off_r + (size_t)4 * 2 * RLEN * 2;  // integer sums [128 gates][128 rows]
     static constexpr size_t off_bar = off_acc + (size_t)T5_NG * T5_M * 4;  // mbarriers, then the TMEM address
-    static constexpr int NBARS = 2 * T5_STAGES + 4;  // full[S], empty[S], done[2], ready[2]
+    static constexpr int NBARS = 2 * T5_STAGES + 5;  // full[S], empty[S], done[2], ready[2], fin
     static constexpr size_t used = off_bar + 8 * NBARS + 8;
     // + 1 KB to align the base; more than half of the SM: one CTA per SM,
     // so the 512 TMEM columns it allocates are always free
@@ -206,11 +207,44 @@ __device__ __forceinline__ bool workers_all(bool ok) {
     return r != 0;
 }
 
-// Grid (N / 128, G / 128, outputs), T5_THREADS threads; dmap: the digits
-// as a [chunks][G][N] bf16 tensor, tile box 64 x 128 x 1, 128-byte swizzle.
+// One work item: 128 output coefficients (m-tile) x 128 gates (g-tile) of
+// one output; m-tiles vary fastest so that CTAs running at the same time
+// share digit tiles in L2.
+struct T5Item {
+    int m0;
+    uint32_t g0;
+    int chunk0;  // first digit polynomial of the output in the tensor map
+    int type;
+    int zi;
+    const uint32_t *key;  // key polynomial 0 of the output
+};
+
+template <int LOGN>
+__device__ __forceinline__ T5Item item_of(const TcArgs &A, uint32_t G, int it) {
+    constexpr int N = 1 << LOGN, MT = N / T5_M;
+    const int GT = (int)(G / T5_NG);
+    T5Item r;
+    r.m0 = (it % MT) * T5_M;
+    const int rest = it / MT;
+    r.g0 = (uint32_t)(rest % GT) * T5_NG;
+    const int z = rest / GT;
+    r.type = z & 1;
+    r.zi = z >> 1;
+    r.chunk0 = (int)(r.zi * (A.dig_zstride / ((size_t)G * N)));
+    r.key = r.type ? A.key[1] + r.zi * A.key_zstride[1] : A.key[0] + r.zi * A.key_zstride[0];
+    return r;
+}
+
+// Persistent: grid min(items, SMs), T5_THREADS threads; CTA b takes items
+// b, b + gridDim.x, ...  Its passes form one sequence gp = 0, 1, ...: pass
+// gp belongs to item gp / (2 nchunks) of the CTA, key polynomial
+// (gp / 2) % nchunks, planes 2 (gp % 2) and 2 (gp % 2) + 1, TMEM half gp % 2,
+// so the prologue and the last drain of an item overlap the MMAs of its
+// neighbours.  dmap: the digits as a [chunks][G][N] bf16 tensor, tile box
+// 64 x 128 x 1, 128-byte swizzle.
 template <int LOGN>
 __global__ void __launch_bounds__(T5_THREADS, 1)
-    tc05_products_kernel(TcArgs A, uint32_t G, const __grid_constant__ CUtensorMap dmap) {
+    tc05_products_kernel(TcArgs A, uint32_t G, int items, const __grid_constant__ CUtensorMap dmap) {
     using L = T5Smem<LOGN>;
     constexpr int N = L::N;
     constexpr int KSTEPS = N / T5_KC;  // digit tiles per key polynomial
@@ -221,23 +255,22 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
     const uint32_t full0 = smem_addr(smem + L::off_bar);  // full[s] = full0 + 8 s
     const uint32_t empty0 = full0 + 8 * T5_STAGES;        // empty[s] = empty0 + 8 s
     const uint32_t done0 = empty0 + 8 * T5_STAGES;        // done[h]: every MMA of a pass on half h
-    const uint32_t ready0 = done0 + 16;                   // ready[h]: half h drained, its next units built
+    const uint32_t ready0 = done0 + 16;                   // ready[h]: half h drained, the units of its next pass built
+    const uint32_t fin = ready0 + 16;                     // the MMA warp's last commit
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::off_bar + 8 * L::NBARS);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int type = blockIdx.z & 1, zi = blockIdx.z >> 1;
-    const int m0 = blockIdx.x * T5_M;
-    const uint32_t g0 = blockIdx.y * T5_NG;
-    const uint32_t *keyz = type ? A.key[1] + zi * A.key_zstride[1] : A.key[0] + zi * A.key_zstride[0];
-    const int chunk0 = (int)(zi * (A.dig_zstride / ((size_t)G * N)));  // first digit polynomial of this output
+    const int nch = A.nchunks, PI = 2 * nch;  // passes per item
+    const int my_items = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int PT = my_items * PI;             // passes of this CTA
     unsigned char *abuf = smem + L::off_a;
     const uint32_t a_base = smem_addr(abuf), b_base = smem_addr(smem + L::off_b);
-    const int P = 2 * A.nchunks;  // passes p = 2 c + h: key polynomial c, planes 2h and 2h + 1
 
     if (tid == 0) {
-        for (int q = 0; q < 2 * T5_STAGES + 2; ++q)
+        for (int q = 0; q < 2 * T5_STAGES + 2; ++q)  // full, empty, done
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * q) : "memory");
         for (int h = 0; h < 2; ++h)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ready0 + 8 * h), "n"(T5_WORKERS) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(fin) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -246,14 +279,6 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (warp < 4) {  // passes 0 and 1: key polynomial 0, all four planes
-        for (int g = 0; g < T5_NG; ++g) sacc[g * T5_M + tid] = 0;
-        build_planes<LOGN>(keyz, m0, rpl, tid, T5_WORKERS);
-        workers_sync();
-        build_units<LOGN>(abuf, rpl, 0, tid);
-        build_units<LOGN>(abuf, rpl, 2, tid);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -261,11 +286,14 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
     bool ok = true;
 
     if (warp == 5) {
-        // producer: tile j = p * KSTEPS + kc into stage j % S once the MMAs
+        // producer: tile j = gp * KSTEPS + kc into stage j % S once the MMAs
         // of tile j - S (same stage) have committed
-        for (int p = 0; p < P && ok; ++p)
+        uint32_t issued = 0;
+        for (int gp = 0; gp < PT && ok; ++gp) {
+            const T5Item I = item_of<LOGN>(A, G, (int)blockIdx.x + (gp / PI) * (int)gridDim.x);
+            const int c = (gp >> 1) % nch;
             for (int kc = 0; kc < KSTEPS; ++kc) {
-                const uint32_t j = (uint32_t)(p * KSTEPS + kc), st = j % T5_STAGES;
+                const uint32_t j = (uint32_t)(gp * KSTEPS + kc), st = j % T5_STAGES;
                 if (j >= T5_STAGES && !mbar_wait(empty0 + 8 * st, ((j / T5_STAGES) - 1) & 1)) ok = false;
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
@@ -273,25 +301,32 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                 }
                 if (lane == 0) {
                     mbar_expect_tx(full0 + 8 * st, (uint32_t)L::stage_bytes);
-                    tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)g0,
-                                chunk0 + (p >> 1), full0 + 8 * st);
+                    tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)I.g0, I.chunk0 + c,
+                                full0 + 8 * st);
                 }
+                issued = j + 1;
                 __syncwarp();
             }
+        }
+        // every copy issued has landed before shared memory can be released
+        // (bounded; in the normal course the MMAs consumed them all)
+        if (lane == 0)
+            for (uint32_t j = issued > T5_STAGES ? issued - T5_STAGES : 0; j < issued; ++j)
+                mbar_wait(full0 + 8 * (j % T5_STAGES), (j / T5_STAGES) & 1);
+        __syncwarp();
     } else if (warp == 4) {
-        // MMA issuer
+        // MMA issuer: pass gp starts once its TMEM half is drained and its
+        // unit arrays are built (ready), then follows the digit tiles (full)
         const uint64_t adesc0 = smem_desc(a_base, 128, 128);
-        for (int p = 0; p < P && ok; ++p) {
-            const int h = p & 1;
-            // passes 0 and 1 were prepared before the roles split; later ones
-            // wait until their TMEM half is drained and their units are built
-            if (p >= 2 && !mbar_wait(ready0 + 8 * h, ((p >> 1) - 1) & 1)) ok = false;
+        for (int gp = 0; gp < PT && ok; ++gp) {
+            const int h = gp & 1;
+            if (!mbar_wait(ready0 + 8 * h, (gp >> 1) & 1)) ok = false;
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 ok = false;
                 break;
             }
             for (int kc = 0; kc < KSTEPS; ++kc) {
-                const uint32_t j = (uint32_t)(p * KSTEPS + kc), st = j % T5_STAGES;
+                const uint32_t j = (uint32_t)(gp * KSTEPS + kc), st = j % T5_STAGES;
                 if (!mbar_wait(full0 + 8 * st, (j / T5_STAGES) & 1)) ok = false;
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
@@ -316,18 +351,37 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                 __syncwarp();
             }
             if (!ok) break;
-            if (lane == 0) mma_commit(done0 + 8 * h);  // every MMA of pass p
+            if (lane == 0) mma_commit(done0 + 8 * h);  // every MMA of pass gp
             __syncwarp();
         }
+        // no MMA of this CTA is in flight past this point (bounded)
+        if (lane == 0) {
+            mma_commit(fin);
+            mbar_wait(fin, 0);
+        }
+        __syncwarp();
     } else {
-        // workers, step p: once pass p - 1 has completed, drain its half;
-        // then build the units of pass p + 1 (same half: its previous MMAs
-        // were pass p - 1) and release it.  The planes of key polynomial
-        // c + 1 are built once both halves of polynomial c have their units.
-        for (int p = 0; p <= P; ++p) {
-            if (p >= 1) {
-                const int hp = (p - 1) & 1;
-                ok = workers_all(mbar_wait(done0 + 8 * hp, ((p - 1) >> 1) & 1));
+        // workers.  Prologue: the unit arrays of passes 0 and 1.  Step gp:
+        // once pass gp - 1 has completed, drain its half into the integer
+        // sums (and write the outputs of its item after its last pass); then
+        // build the units of pass gp + 1 (same half: its previous MMAs were
+        // pass gp - 1) and release it.  The planes of key polynomial s + 1
+        // (s = gp / 2 counts the CTA's key polynomials) are built once both
+        // halves of polynomial s have their units.
+        {
+            const T5Item I = item_of<LOGN>(A, G, (int)blockIdx.x);
+            build_planes<LOGN>(I.key, I.m0, rpl, tid, T5_WORKERS);
+            workers_sync();
+            for (int h = 0; h < 2 && h < PT; ++h) {
+                build_units<LOGN>(abuf, rpl, 2 * h, tid);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(ready0 + 8 * h) : "memory");
+            }
+        }
+        for (int gp = 0; gp <= PT; ++gp) {
+            if (gp >= 1) {
+                const int pp = gp - 1, hp = pp & 1, lp = pp % PI;  // the drained pass, its half, its index in the item
+                ok = workers_all(mbar_wait(done0 + 8 * hp, (pp >> 1) & 1));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
@@ -339,44 +393,47 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        const uint32_t v = (uint32_t)__float2int_rn(__uint_as_float(r0[i])) +
-                                           ((uint32_t)__float2int_rn(__uint_as_float(r1[i])) << 8);
-                        sacc[(q * 32 + i) * T5_M + tid] += v << (16 * hp);
+                        const uint32_t v = ((uint32_t)__float2int_rn(__uint_as_float(r0[i])) +
+                                            ((uint32_t)__float2int_rn(__uint_as_float(r1[i])) << 8))
+                                           << (16 * hp);
+                        uint32_t &a = sacc[(q * 32 + i) * T5_M + tid];
+                        a = lp == 0 ? v : a + v;
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                if (lp == PI - 1) {
+                    // row r' = tid holds coefficient m0 + 127 - tid of every gate
+                    const T5Item I = item_of<LOGN>(A, G, (int)blockIdx.x + (pp / PI) * (int)gridDim.x);
+                    int32_t *dst = (I.type ? A.dst[1] : A.dst[0]) + I.zi * A.dst_zstride + (I.m0 + 127 - tid) +
+                                   (size_t)I.g0 * A.dst_stride;
+#pragma unroll 1
+                    for (int g = 0; g < T5_NG; g += 16) {
+                        uint32_t old[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            old[i] = A.accumulate ? (uint32_t)dst[(size_t)(g + i) * A.dst_stride] : 0u;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            dst[(size_t)(g + i) * A.dst_stride] = (int32_t)(old[i] + sacc[(g + i) * T5_M + tid]);
+                    }
+                }
             }
-            const int q = p + 1, cq = q >> 1, hq = q & 1;
-            if (q >= 2 && q < P) {
-                workers_sync();  // the planes of key polynomial cq are complete
+            const int q = gp + 1, s = q >> 1, hq = q & 1;
+            if (q >= 2 && q < PT) {
+                workers_sync();  // the planes of key polynomial s are complete
                 build_units<LOGN>(abuf, rpl, 2 * hq, tid);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(ready0 + 8 * hq) : "memory");
             }
-            if (hq == 1 && cq + 1 < A.nchunks) {
-                workers_sync();  // every unit of key polynomial cq is built: the planes may be replaced
-                build_planes<LOGN>(keyz + (size_t)(cq + 1) * N, m0, rpl, tid, T5_WORKERS);
+            if (hq == 1 && 2 * (s + 1) < PT) {
+                workers_sync();  // every unit of key polynomial s is built: the planes may be replaced
+                const T5Item I = item_of<LOGN>(A, G, (int)blockIdx.x + ((s + 1) / nch) * (int)gridDim.x);
+                build_planes<LOGN>(I.key + (size_t)((s + 1) % nch) * N, I.m0, rpl, tid, T5_WORKERS);
             }
         }
     }
-    if (__syncthreads_and(ok)) {
-        if (warp < 4) {
-            // row r' = tid holds coefficient m0 + 127 - tid of every gate
-            int32_t *dst = (type ? A.dst[1] : A.dst[0]) + zi * A.dst_zstride;
-            const int m = m0 + 127 - tid;
-            for (int g = 0; g < T5_NG; ++g) {
-                int32_t *d = dst + (size_t)(g0 + g) * A.dst_stride + m;
-                const uint32_t v = sacc[g * T5_M + tid];
-                *d = A.accumulate ? (int32_t)((uint32_t)*d + v) : (int32_t)v;
-            }
-        }
-    } else if (tid == 0) {
-        atomicCAS(&g_tc05_error, 0u, 1u + blockIdx.x + 1024u * blockIdx.y);
-        // let copies and MMAs still in flight land before their memory goes away (bounded)
-        for (int q = 0; q < T5_STAGES; ++q) mbar_wait(full0 + 8 * q, 0);
-        mbar_wait(done0, 0);
-    }
-    __syncthreads();
+    if (!__syncthreads_and(ok) && tid == 0) atomicCAS(&g_tc05_error, 0u, 1u + blockIdx.x);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(T5_TMEM_COLS)
                      : "memory");
@@ -418,9 +475,14 @@ static cudaError_t launch_tc05(const TcArgs &A, uint32_t G, int outputs, cudaStr
         return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tc05_products_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)T5Smem<LOGN>::bytes);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    tc05_products_kernel<LOGN><<<dim3(N / T5_M, G / T5_NG, outputs), T5_THREADS, T5Smem<LOGN>::bytes, st>>>(A, G,
-                                                                                                           map);
+    // one CTA per SM (its shared memory and TMEM take the SM), each looping over items
+    const int items = (N / T5_M) * (int)(G / T5_NG) * outputs;
+    const int grid = items < sms ? items : sms;
+    tc05_products_kernel<LOGN><<<grid, T5_THREADS, T5Smem<LOGN>::bytes, st>>>(A, G, items, map);
     return cudaGetLastError();
 }
 
