@@ -347,7 +347,7 @@ def run_ours(args):
                            for t, a, b in zip(ts, x1.astype(int), x2.astype(int))], np.uint8)
             dt_, d1, d2 = tdev(ts.astype(np.uint8)), tdev(e1), tdev(e2)
             do = torch.zeros((Gs, ck.W), dtype=torch.int32, device="cuda")
-            for form in ("ntt", "ntt2", "fft", "tc"):
+            for form in args.sweep_forms.split(","):
                 Gf = Gs if form != "tc" else 2048  # the O(N^2) form: one 2048-gate wave
                 ck.set_form(form)
                 ck.autotune(1024)
@@ -512,6 +512,8 @@ def main():
                     help="blind-rotation variant to use instead of autotuning (-1: autotune)")
     ap.add_argument("--sweep", action="store_true",
                     help="also time every product form at 2, 4 and 8 parties (8192 joint-key gates each)")
+    ap.add_argument("--sweep-forms", default="ntt,ntt2,fft,tc",
+                    help="comma-separated product forms the sweep times")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
