@@ -81,6 +81,21 @@ def test_tc_products_several_gate_tiles(gpu_ready, engine):
     assert np.array_equal(_run_tc(keys, digits, engine), negacyclic_sum_int64(keys, digits))
 
 
+@pytest.mark.parametrize("N,G,nch", [(1024, 5120, 2), (256, 128 * 200, 3)])
+def test_tc05_products_several_items_per_cta(gpu_ready, N, G, nch):
+    """The persistent tcgen05 kernel with more work items than SMs (320 and
+    400 items of 128 coefficients x 128 gates), so every CTA runs passes of
+    two or three items back to back: sampled gates (first and last of
+    several gate tiles, random others) word for word."""
+    rng = np.random.default_rng(13 + N)
+    keys = rng.integers(0, 2 ** 32, size=(nch, N), dtype=np.uint64).astype(np.uint32)
+    digits = rng.integers(-128, 128, size=(nch, G, N)).astype(np.int8)
+    got = _run_tc(keys, digits, engine=1)
+    idx = np.unique(np.concatenate([[0, 127, 128, 255, G // 2, G - 129, G - 128, G - 1],
+                                    rng.integers(0, G, size=40)]))
+    assert np.array_equal(got[idx], negacyclic_sum_int64(keys, digits[:, idx, :]))
+
+
 def test_tc_products_rejects_bad_shapes(gpu_ready):
     import torch
     from paper_2205_05825_gb300 import binding as B
