@@ -125,8 +125,8 @@ cudaError_t launch_bootstrap_tc(const LaunchShape &S, const DeviceKeys &K, const
                                 const uint32_t *ct_b, const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,
                                 uint32_t *acc_out, uint32_t count, cudaStream_t st);
 bool tc_shape_supported(const LaunchShape &S);
-// One pass of a Toeplitz product kernel of the tensor form: output z of the
-// grid's z dimension is dst[type] + (z >> 1) * dst_zstride (row g at
+// One launch of a Toeplitz product kernel of the tensor form: output z
+// (0 <= z < outputs) is dst[type] + (z >> 1) * dst_zstride (row g at
 // g * dst_stride words), type = z & 1, the sum over nchunks products of
 // key[type] + (z >> 1) * key_zstride[type] + c * N (torus32 words) with the
 // digits dig + (z >> 1) * dig_zstride + c * G * N ([G][N] bf16 bit patterns).
@@ -143,7 +143,8 @@ struct TcArgs {
     int dig_chunks;  // digit polynomials in the whole dig array (for the tcgen05 engine's tensor map)
 };
 // The tcgen05 engine of those products (mk_tensor_tc05.cu): G a multiple of
-// 128.  tc05_error reads (and optionally clears) the timeout record of its
+// 128; one persistent CTA per SM over (coefficient tile, gate tile, output)
+// items of 128 x 128.  tc05_error reads (and optionally clears) the timeout record of its
 // bounded waits (0: none).
 cudaError_t launch_products_tc05(const TcArgs &A, uint32_t N, uint32_t G, int outputs, cudaStream_t st);
 cudaError_t tc05_error(unsigned int *code, bool clear);
