@@ -3,9 +3,9 @@
  *
  * The calls follow the paper's statement of the problem (Jiang et al.,
  * "Privacy-Preserving Distributed Machine Learning Made Faster",
- * arXiv 2205.05825): MKTFHE.Setup / KeyGen / SymEnc / SymDec (Sec. 2.2),
- * the bootstrapped gates of Sec. 3.1 (Eq. 6-11 and the NAND of Sec. 2.2),
- * MKNOT (Eq. 8) and the k-bit two's-complement operators of Sec. 3.3-3.5
+ * arXiv 2205.05825): MKTFHE.Setup / KeyGen / SymEnc / SymDec (Sec. 3.2),
+ * the bootstrapped gates of Sec. 4.1 (Eq. 6-11 and the NAND of Sec. 3.2),
+ * MKNOT (Eq. 8) and the k-bit two's-complement operators of Sec. 4.3-4.5
  * (Algorithms 3-6).
  *
  * Conventions shared by every call
@@ -13,7 +13,7 @@
  *  - Torus elements are uint32 (x stands for x / 2^32).
  *  - A multi-key LWE ciphertext is one row uint32[k*n + 1] laid out as
  *    (a_1 | a_2 | ... | a_k | b): party blocks of n words, then b.  Its phase
- *    is b + sum_i <a_i, s_i>; a bit m is encoded as m/4 (Sec. 2.2, SymEnc).
+ *    is b + sum_i <a_i, s_i>; a bit m is encoded as m/4 (Sec. 3.2, SymEnc).
  *  - Batches are row-major [count][k*n + 1].  k-bit integers are LSB-first
  *    rows of bit ciphertexts, two's complement: [pairs][kbits][k*n + 1].
  *  - Pointers named d_* are device pointers on the context's device, owned by
@@ -48,7 +48,7 @@ extern "C" {
 #define MK_EFORMAT (-7)  /* key blob has a bad header, size or checksum */
 
 /* ---------------------------------------------------------------- params */
-/* mkparams (Sec. 2.1, Table 7): LWE dimension n, ring dimension N, party
+/* mkparams (Sec. 3.1, Table 7): LWE dimension n, ring dimension N, party
  * count k, bootstrapping gadget base B = 2^bg_bit of length d, key-switching
  * base B' = 2^ks_bit of length t (Table 7's d'), and the Gaussian noise
  * standard deviations (torus units) of LWE and RLWE samples. */
@@ -72,7 +72,7 @@ int mk_params_preset(int preset, uint32_t k, mk_params *out);
 /* ---------------------------------------------------------------- context */
 typedef struct mk_ctx mk_ctx;
 
-/* MKTFHE.Setup (Sec. 2.2): create a context for `params`, derive the common
+/* MKTFHE.Setup (Sec. 3.2): create a context for `params`, derive the common
  * reference string a in T_N[X]^d from crs_seed, bind CUDA device `device`
  * and stream `stream` (a cudaStream_t; NULL = the legacy default stream).
  * device = -1 makes a host-only context: key generation, encryption,
@@ -169,7 +169,7 @@ const char *mk_last_error(const mk_ctx *ctx);
 int mk_sync(mk_ctx *ctx);
 
 /* ---------------------------------------------------------------- keys */
-/* MKTFHE.KeyGen (Sec. 2.2) for party `party` (0-based) from `seed`: the TLWE
+/* MKTFHE.KeyGen (Sec. 3.2) for party `party` (0-based) from `seed`: the TLWE
  * secret s in {0,1}^n, the RLWE secret z in {0,1}^N, the public key
  * b = -z*a + e, the bootstrapping key BK = {UniEnc(s_j; z)}_j and the
  * key-switching key KS.  Secrets stay in host memory of the context; public
@@ -201,7 +201,7 @@ int mk_save_keys(const mk_ctx *ctx, int include_secrets, void *h_blob, size_t ca
 int mk_load_keys(mk_ctx *ctx, const void *h_blob, size_t len);
 
 /* ---------------------------------------------------------------- enc/dec */
-/* MKTFHE.SymEnc (Sec. 2.2) by party `party` of count bits (0/1 bytes) into
+/* MKTFHE.SymEnc (Sec. 3.2) by party `party` of count bits (0/1 bytes) into
  * h_ct [count][k*n + 1], extended to the multi-key layout (other parties'
  * blocks zero).  b = -<a, s> + m/4 + e; a and e from Philox streams of seed. */
 int mk_encrypt(mk_ctx *ctx, uint32_t party, const uint8_t *h_bits, size_t count, uint64_t seed,
@@ -210,7 +210,7 @@ int mk_encrypt(mk_ctx *ctx, uint32_t party, const uint8_t *h_bits, size_t count,
  * party's secret.  Used to make all k*n blind-rotation steps active. */
 int mk_encrypt_joint(mk_ctx *ctx, const uint8_t *h_bits, size_t count, uint64_t seed, uint32_t *h_ct);
 
-/* MKTFHE.SymDec (Sec. 2.2): with every party's secret, the bit m minimising
+/* MKTFHE.SymDec (Sec. 3.2): with every party's secret, the bit m minimising
  * |b + sum_i <a_i, s_i> - m/4|.  `ct` is a host pointer if on_device == 0,
  * else a device pointer (copied back, synchronising the stream). */
 int mk_decrypt(mk_ctx *ctx, const uint32_t *ct, size_t count, int on_device, uint8_t *h_bits);
@@ -220,9 +220,9 @@ int mk_phase(mk_ctx *ctx, const uint32_t *ct, size_t count, int on_device, uint3
 /* ---------------------------------------------------------------- gates */
 enum { MK_AND = 0, MK_OR = 1, MK_NAND = 2, MK_NOR = 3, MK_XOR = 4, MK_XNOR = 5 };
 
-/* Multi-key bootstrapped gates (Sec. 3.1): for g < count,
+/* Multi-key bootstrapped gates (Sec. 4.1): for g < count,
  *   d_out[g] = KeySwitch(GB(lin(type, d_a[g], d_b[g])))
- * with the linear part of Eq. 6 (AND), Eq. 7 (OR), Sec. 2.2 (NAND: 5/8 - c1 - c2),
+ * with the linear part of Eq. 6 (AND), Eq. 7 (OR), Sec. 3.2 (NAND: 5/8 - c1 - c2),
  * Eq. 9 (NOR, constant 3/8), Eq. 10 (XOR), Eq. 11 (XNOR: 1/2 + 2(c1 - c2)).
  * mk_gate applies one type to every gate; mk_gates reads a per-gate type
  * (uint8, device).  d_out may not alias d_a or d_b.  Needs every party's
@@ -243,7 +243,7 @@ int mk_gates_lin(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const ui
 int mk_not(mk_ctx *ctx, const uint32_t *d_a, uint32_t *d_out, size_t count);
 
 /* ---------------------------------------------------------------- operators */
-/* k-bit two's-complement operators (Sec. 2.3, Sec. 3.3-3.5, Algorithms 3-6)
+/* k-bit two's-complement operators (Sec. 3.3, Sec. 4.3-4.5, Algorithms 3-6)
  * as netlists of the bootstrapped gates, evaluated level by level: every
  * level of the netlist is one batched bootstrap + key-switch launch over all
  * its gates of all `pairs` operand pairs (gates of one level are
@@ -282,7 +282,7 @@ int mk_circuit_netlist(int op, uint32_t kbits, mk_gate_rec *gates, uint32_t gate
 
 /* ---------------------------------------------------------------- serving */
 /* Continuous batching of operator requests from several clients (the paper's
- * cloud server evaluating participants' circuits, Sec. 4.5).  Every admitted
+ * cloud server evaluating participants' circuits, Sec. 5.5).  Every admitted
  * request keeps its wire ciphertexts in one device pool of `pool_rows`
  * ciphertext rows; mk_server_step runs one wave: one batched bootstrap +
  * key-switch launch over at most `wave_gates` ready gates of all running
@@ -317,7 +317,7 @@ int mk_server_stats(const mk_server *srv, uint64_t *waves, uint64_t *gates, uint
  *   first max_steps CMux steps (-1 = all k*n), from d_abar.
  * mk_stage_bootstrap: d_ext[g] = SampleExtract(blind rotation) + 1/8, an LWE
  *   of dimension k*N + 1 under (z_1..z_k).
- * mk_stage_keyswitch: MKKeySwitch (Sec. 2.2) of d_ext into d_out. */
+ * mk_stage_keyswitch: MKKeySwitch (Sec. 3.2) of d_ext into d_out. */
 int mk_stage_modswitch(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b,
                        uint32_t *d_abar, size_t count);
 int mk_stage_blind_rotate(mk_ctx *ctx, const uint32_t *d_abar, size_t count, int64_t max_steps,
@@ -389,7 +389,7 @@ int mk_measure_butterfly_rate(int device, void *stream, int form, uint32_t iters
  * The call allocates a bf16 copy of the digits, runs on `stream` and
  * synchronises it.  The same engine numbers select the tensor form's engine
  * as its variant (mk_ctx_set_variant; mk_autotune times both).
- * No paper counterpart: the negacyclic product of Section 2 (the hybrid
+ * No paper counterpart: the negacyclic product of Sec. 3.1-3.2 (the hybrid
  * product's inner step) isolated for testing the tensor form. */
 int mk_tc_negacyclic(int device, void *stream, uint32_t N, uint32_t G, uint32_t nchunks, const uint32_t *keys,
                      const int8_t *digits, int32_t *out, int engine);

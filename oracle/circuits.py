@@ -1,8 +1,8 @@
 """Netlists of the k-bit two's-complement operators (test infrastructure only).
 
-Written from the paper's descriptions (Sec. 2.3, Sec. 3.3-3.5, Algorithms 3-6)
+Written from the paper's descriptions (Sec. 3.3, Sec. 4.3-4.5, Algorithms 3-6)
 under these readings:
-  - full adder (Sec. 2.3, Alg. 3): t = a XOR b; s = t XOR c;
+  - full adder (Sec. 3.3, Alg. 3): t = a XOR b; s = t XOR c;
     cout = (a AND b) OR (t AND c) -- 5 bootstrapped gates per bit, carry-in
     0, the last carry computed and dropped, so 5k gates as in Table 3;
   - subtractor (Alg. 5): a + NOT(b) + 1, NOT folded into the next gate's

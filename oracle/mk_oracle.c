@@ -9,10 +9,10 @@
  * Everything here follows the paper (Jiang et al., "Privacy-Preserving
  * Distributed Machine Learning Made Faster", arXiv 2205.05825) and the MKTFHE
  * scheme it builds on, step by step, with no blocking, fusion or reordering:
- *   - notation, torus T = R/Z, T_N[X] = R[X]/(X^N+1) mod 1: Sec. 2.1
- *   - MKTFHE.Setup / KeyGen / SymEnc / SymDec / MKKeySwitch / NAND: Sec. 2.2
- *   - TFHE gate constants: Sec. 2.2 (bullet list of TFHE.Boots*)
- *   - multi-key gates: Sec. 3.1, Eq. 6-11; LweAdd Algorithm 1, LweMul
+ *   - notation, torus T = R/Z, T_N[X] = R[X]/(X^N+1) mod 1: Sec. 3.1
+ *   - MKTFHE.Setup / KeyGen / SymEnc / SymDec / MKKeySwitch / NAND: Sec. 3.2
+ *   - TFHE gate constants: Sec. 3.2 (bullet list of TFHE.Boots*)
+ *   - multi-key gates: Sec. 4.1, Eq. 6-11; LweAdd Algorithm 1, LweMul
  *     Algorithm 2; operation matrix Table 1
  *   - parameters: Table 7
  * Torus elements are held as uint32 (x stands for x / 2^32); all arithmetic
@@ -22,12 +22,12 @@
  *
  * Readings of points the paper leaves open (the paper names UniEnc, the
  * hybrid product and the multi-key key switch but does not define them):
- *   R1  phase convention: phi = b + sum_i <a_i, s_i> (Sec. 2.2, SymEnc/SymDec);
+ *   R1  phase convention: phi = b + sum_i <a_i, s_i> (Sec. 3.2, SymEnc/SymDec);
  *       the same "+" sign for RLWE: phi = c_0 + sum_j c_j z_j.
  *   R2  bit m is encoded as m/4 (SymEnc, scaling factor 1/4).  The bootstrap
  *       maps input phase in [1/4, 3/4) to 1/4 and the rest to 0: a -1/4 shift
  *       of b, a sign test by the test vector of constant 1/8, then +1/8.
- *       This is the only window under which the NAND constant 5/8 (Sec. 2.2),
+ *       This is the only window under which the NAND constant 5/8 (Sec. 3.2),
  *       AND (Eq. 6), OR (Eq. 7), XOR (Eq. 10) and NOT (Eq. 8) are all correct.
  *   R3  NOR and XNOR as printed (Eq. 9: 1/8 - c1 - c2; Eq. 11:
  *       1/4 - 2(c1 - c2)) fail their truth tables under R2; this oracle uses
@@ -137,7 +137,7 @@ enum {
 };
 
 /* ------------------------------------------------------------------------- */
-/* Polynomials in T_N[X] = R[X]/(X^N + 1) mod 1 (Sec. 2.1), coefficients     */
+/* Polynomials in T_N[X] = R[X]/(X^N + 1) mod 1 (Sec. 3.1), coefficients     */
 /* held as uint32 (torus32) or as small integers cast to uint32.              */
 /* ------------------------------------------------------------------------- */
 
@@ -207,7 +207,7 @@ static void gadget_decompose_poly(const orc_params *P, const uint32_t *c, uint32
 }
 
 /* ------------------------------------------------------------------------- */
-/* Key generation: MKTFHE.Setup / MKTFHE.KeyGen (Sec. 2.2), readings R4, R7.  */
+/* Key generation: MKTFHE.Setup / MKTFHE.KeyGen (Sec. 3.2), readings R4, R7.  */
 /* Layouts (uint32):                                                          */
 /*   crs  [d][N]                     the common reference string a            */
 /*   s    [n]  (0/1), z [N] (0/1)    TLWE and RLWE secrets of one party       */
@@ -291,7 +291,7 @@ void orc_keygen_party(const orc_params *P, const uint32_t *crs, uint64_t seed, u
 }
 
 /* ------------------------------------------------------------------------- */
-/* MKTFHE.SymEnc / SymDec (Sec. 2.2).  A multi-key ciphertext is laid out as  */
+/* MKTFHE.SymEnc / SymDec (Sec. 3.2).  A multi-key ciphertext is laid out as  */
 /* uint32[k*n + 1] = (a_1 | a_2 | ... | a_k | b); ciphertext extension of a   */
 /* single-key ciphertext of party p zero-fills every other block.             */
 /* ------------------------------------------------------------------------- */
@@ -352,7 +352,7 @@ void orc_decrypt(const orc_params *P, const uint32_t *s_all, const uint32_t *ct,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Ciphertext-level linear operations (Sec. 3.2).                             */
+/* Ciphertext-level linear operations (Sec. 4.2).                             */
 /* ------------------------------------------------------------------------- */
 /* ModToT: a fraction num/den of the torus as torus32 (den a power of two). */
 uint32_t orc_mod_to_t(int32_t num, uint32_t den) {
@@ -366,7 +366,7 @@ void orc_lwe_add(const orc_params *P, const uint32_t *c1, const uint32_t *c2, ui
     for (size_t x = 0; x < W; ++x) out[x] = c1[x] + c2[x];
 }
 
-/* LweSub (provided by MKTFHE, Sec. 3.1): c1 - c2 element by element. */
+/* LweSub (provided by MKTFHE, Sec. 4.1): c1 - c2 element by element. */
 void orc_lwe_sub(const orc_params *P, const uint32_t *c1, const uint32_t *c2, uint32_t *out) {
     const size_t W = (size_t)P->k * P->n + 1;
     for (size_t x = 0; x < W; ++x) out[x] = c1[x] - c2[x];
@@ -391,7 +391,7 @@ enum { ORC_AND = 0, ORC_OR = 1, ORC_NAND = 2, ORC_NOR = 3, ORC_XOR = 4, ORC_XNOR
 /* The linear part of each bootstrapped gate (Table 1 lists the operations):
  *   AND  (Eq. 6):  (0,-1/8) + c1 + c2                 LweAdd, ModToT
  *   OR   (Eq. 7):  (0, 1/8) + c1 + c2                 LweAdd, ModToT
- *   NAND (Sec. 2.2, TFHE.BootsNAND): (0, 5/8) - c1 - c2   LweSub, ModToT
+ *   NAND (Sec. 3.2, TFHE.BootsNAND): (0, 5/8) - c1 - c2   LweSub, ModToT
  *   NOR  (Eq. 9, constant per reading R3): (0, 3/8) - c1 - c2
  *   XOR  (Eq. 10): 2 * (c1 - c2)                      LweSub, LweMul
  *   XNOR (Eq. 11, per reading R3): (0, 1/2) + 2 * (c1 - c2)
@@ -464,7 +464,7 @@ void orc_not(const orc_params *P, const uint32_t *c, uint32_t *out) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* Gate bootstrapping GB (Sec. 2.2): evaluate the decryption circuit.         */
+/* Gate bootstrapping GB (Sec. 3.2): evaluate the decryption circuit.         */
 /* ------------------------------------------------------------------------- */
 
 /* Modulus switch of every word to Z_{2N}: round(x * 2N / 2^32) mod 2N. */
@@ -580,7 +580,7 @@ void orc_bootstrap(const orc_params *P, const uint32_t *c, const uint32_t *crs,
     free(acc);
 }
 
-/* MKTFHE.MKKeySwitch (Sec. 2.2, reading R7): LWE of dimension k*N under
+/* MKTFHE.MKKeySwitch (Sec. 3.2, reading R7): LWE of dimension k*N under
  * (z_1..z_k) -> LWE of dimension k*n under (s_1..s_k). */
 void orc_keyswitch(const orc_params *P, const uint32_t *const *kss, const uint32_t *lwe_in,
                    uint32_t *out) {
@@ -606,7 +606,7 @@ void orc_keyswitch(const orc_params *P, const uint32_t *const *kss, const uint32
     }
 }
 
-/* One multi-key bootstrapped gate (MKTFHE.NAND pattern, Sec. 2.2 / 3.1):
+/* One multi-key bootstrapped gate (MKTFHE.NAND pattern, Sec. 3.2 / 3.1):
  * linear combination -> GB -> MKKeySwitch. */
 int orc_gate(const orc_params *P, int type, const uint32_t *c1, const uint32_t *c2,
              const uint32_t *crs, const uint32_t *const *pks, const uint32_t *const *bks,

@@ -1,7 +1,7 @@
 """ctypes wrapper of the CPU oracle (test infrastructure only).
 
 The oracle is the plain, slow reference implementation of multi-key TFHE gate
-bootstrapping written from the paper (arXiv 2205.05825, Sec. 2.2, Sec. 3.1-3.2,
+bootstrapping written from the paper (arXiv 2205.05825, Sec. 3.2, Sec. 4.1-4.2,
 Eq. 6-11, Algorithms 1-2, Table 1, Table 7); see ``mk_oracle.c`` for the
 definitions and the readings of points the paper leaves open.  Only the test
 suite, the smoke check and the CPU-baseline leg of the benchmark may import
@@ -179,7 +179,7 @@ def key_shapes(params):
 
 
 def keygen(params, crs_seed, party_seeds, nthreads=None):
-    """MKTFHE.Setup + MKTFHE.KeyGen for every party (Sec. 2.2)."""
+    """MKTFHE.Setup + MKTFHE.KeyGen for every party (Sec. 3.2)."""
     nthreads = default_threads() if nthreads is None else nthreads
     sh = key_shapes(params)
     crs = np.zeros(sh["crs"], np.uint32)

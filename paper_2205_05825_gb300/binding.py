@@ -419,7 +419,7 @@ class Context:
 
 
 # Linear-part records (cst, s1, s2) of the six bootstrapped gates, for
-# mk_gates_lin: Eq. 6 (AND), Eq. 7 (OR), Sec. 2.2 (NAND), Eq. 9 (NOR, 3/8),
+# mk_gates_lin: Eq. 6 (AND), Eq. 7 (OR), Sec. 3.2 (NAND), Eq. 9 (NOR, 3/8),
 # Eq. 10 (XOR), Eq. 11 (XNOR, 1/2 + 2(c1 - c2)).
 GATE_LIN = {0: (0xE0000000, 1, 1), 1: (0x20000000, 1, 1), 2: (0xA0000000, -1, -1),
             3: (0x60000000, -1, -1), 4: (0, 2, -2), 5: (0x80000000, 2, -2)}

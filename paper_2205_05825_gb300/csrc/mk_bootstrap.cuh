@@ -28,9 +28,9 @@
 //     product is three multiply-adds without a second table.
 // Both give the exact integer product sums, hence identical ciphertexts.
 //
-// Paper steps (arXiv 2205.05825): gate linear part (Sec. 3.1, Eq. 6-11,
-// Algorithms 1-2), gate bootstrapping GB (Sec. 2.2).  The hybrid product
-// follows the MKTFHE construction the paper builds on (named in Sec. 2.2):
+// Paper steps (arXiv 2205.05825): gate linear part (Sec. 4.1, Eq. 6-11,
+// Algorithms 1-2), gate bootstrapping GB (Sec. 3.2).  The hybrid product
+// follows the MKTFHE construction the paper builds on (named in Sec. 3.2):
 // u_j = g^-1(c_j); v = -<u_0, a> + sum_{j>=1} <u_j, pk_j>; w = g^-1(v);
 // c'_j = <u_j, d>; c'_0 += <w, f0>; c'_i += <w, f1>.
 #pragma once

@@ -5,7 +5,7 @@
 // the (k+2)(d+1) transforms of every CMux step one after the other.  For a
 // small batch that leaves most SMs idle and the gate's latency is that whole
 // chain.  Here CTA jj of a cluster of k+1 owns ACC_jj (shared memory) and, per
-// CMux step of the hybrid product (Sec. 2.2; u_jj = g^-1((X^-e - 1) ACC_jj),
+// CMux step of the hybrid product (Sec. 3.2; u_jj = g^-1((X^-e - 1) ACC_jj),
 // v = sum_jj <u_jj, A_jj>, w = g^-1(v), ACC_jj += <u_jj, d>, ACC_0 += <w, f0>,
 // ACC_i += <w, f1>):
 //   1. every CTA transforms the digits of its own (X^-e - 1) ACC_jj and

@@ -1,5 +1,5 @@
-// mk_circuits.cpp -- k-bit two's-complement operators (Sec. 2.3 and
-// Sec. 3.3-3.5 of arXiv 2205.05825, Algorithms 3-6) as netlists of the
+// mk_circuits.cpp -- k-bit two's-complement operators (Sec. 3.3 and
+// Sec. 4.3-4.5 of arXiv 2205.05825, Algorithms 3-6) as netlists of the
 // bootstrapped gates, and their levelised evaluation on the GPU.
 //
 // Netlist definition (wire numbering and construction order are part of it):
@@ -17,7 +17,7 @@
 //     mixed-sign terms, constant ones at columns k and 2k-1), column
 //     compression with full adders, a final ripple addition; 2k-bit product;
 //   divider (Alg. 6): compensation devices to magnitudes, a non-restoring
-//     array of CAS cells (Sec. 3.5: out = a XOR ((b XOR p) XOR c),
+//     array of CAS cells (Sec. 4.5: out = a XOR ((b XOR p) XOR c),
 //     cout = ((a OR c) AND (b XOR p)) OR (a AND c)), a remainder correction,
 //     compensation back; quotient sign = sign(a) XOR sign(b), remainder with
 //     a's sign (truncating division).

@@ -1,5 +1,5 @@
 // mk_host.cpp -- host runtime of the multi-key TFHE library: parameters,
-// counter-based randomness, key generation (MKTFHE.Setup / KeyGen, Sec. 2.2
+// counter-based randomness, key generation (MKTFHE.Setup / KeyGen, Sec. 3.2
 // of arXiv 2205.05825), SymEnc / SymDec, key layout and upload for the
 // kernels, and the C ABI declared in include/mk_tfhe.h.
 #include <algorithm>

@@ -1,6 +1,6 @@
 // mk_kernels.cu -- sm_103a kernels of multi-key TFHE gates other than the
 // blind rotation (which lives in mk_bootstrap.cuh): modulus switch stage,
-// MKKeySwitch (Sec. 2.2 of arXiv 2205.05825), MKNOT (Eq. 8), gate
+// MKKeySwitch (Sec. 3.2 of arXiv 2205.05825), MKNOT (Eq. 8), gate
 // descriptors, and the dispatch to the per-ring-dimension blind rotation.
 #include "mk_internal.h"
 
@@ -156,7 +156,7 @@ __global__ void not_kernel(uint32_t W, const uint32_t *__restrict__ in, uint32_t
     }
 }
 
-// (cst, s1, s2) of each gate type: AND Eq. 6, OR Eq. 7, NAND Sec. 2.2,
+// (cst, s1, s2) of each gate type: AND Eq. 6, OR Eq. 7, NAND Sec. 3.2,
 // NOR Eq. 9 (constant 3/8), XOR Eq. 10, XNOR Eq. 11 (1/2 + 2(c1 - c2)).
 __constant__ uint32_t c_gate_cst[6] = {0xE0000000u, 0x20000000u, 0xA0000000u, 0x60000000u, 0x0u, 0x80000000u};
 __constant__ int32_t c_gate_s1[6] = {1, 1, -1, -1, 2, 2};

@@ -1,5 +1,5 @@
 // mk_server.cpp -- continuous-batching evaluation of many k-bit operator
-// requests (Sec. 3.3-3.5 operators) from several clients.
+// requests (Sec. 4.3-4.5 operators) from several clients.
 //
 // Every admitted request keeps its wire ciphertexts in one device pool (rows
 // of k*n+1 words, a first-fit row allocator).  A wave is one batched

@@ -1,4 +1,4 @@
-"""k-bit two's-complement operators (Sec. 2.3, Sec. 3.3-3.5, Alg. 3-6).
+"""k-bit two's-complement operators (Sec. 3.3, Sec. 4.3-4.5, Alg. 3-6).
 
 Pins: the oracle's netlists against native integer arithmetic (exhaustive
 for 2..5-bit operands, random pairs at 8 and 16 bits); the library's netlists

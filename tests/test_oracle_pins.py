@@ -197,13 +197,13 @@ def test_linear_ops_are_exact_on_phases(tiny_keys):
 
 
 def _window_bit(phase):
-    """The bootstrap's decision (reading of Sec. 2.2 with the 1/4 encoding):
+    """The bootstrap's decision (reading of Sec. 3.2 with the 1/4 encoding):
     1 iff the phase lies in [1/4, 3/4)."""
     return int(((phase - (1 << 30)) & 0xFFFFFFFF) < (1 << 31))
 
 
 def test_gate_constants_against_truth_tables(tiny_keys):
-    """The linear part of every gate (Eq. 6-11, NAND of Sec. 2.2) puts the
+    """The linear part of every gate (Eq. 6-11, NAND of Sec. 3.2) puts the
     phase of noiseless inputs inside the window [1/4, 3/4) exactly when the
     gate's truth table says 1, at distance >= 1/8 from the window edges."""
     P, K = tiny_keys
