@@ -210,6 +210,15 @@ int mk_encrypt(mk_ctx *ctx, uint32_t party, const uint8_t *h_bits, size_t count,
  * party's secret.  Used to make all k*n blind-rotation steps active. */
 int mk_encrypt_joint(mk_ctx *ctx, const uint8_t *h_bits, size_t count, uint64_t seed, uint32_t *h_ct);
 
+/* A noiseless ciphertext of each public bit: zero mask, zero noise, b = m/4
+ * (the encoding of SymEnc, Sec. 3.2).  It decrypts to the bit under every
+ * set of keys and needs no secret: the operator circuits use it for their
+ * constant wires, and a server for public operands of the encrypted
+ * application (a data count, a learning rate, a zoom factor; Sec. 4.6).
+ * Only the lowest bit of each h_bits byte is read; h_ct: host
+ * [count][k*n + 1]. */
+int mk_trivial(mk_ctx *ctx, const uint8_t *h_bits, size_t count, uint32_t *h_ct);
+
 /* MKTFHE.SymDec (Sec. 3.2): with every party's secret, the bit m minimising
  * |b + sum_i <a_i, s_i> - m/4|.  `ct` is a host pointer if on_device == 0,
  * else a device pointer (copied back, synchronising the stream). */

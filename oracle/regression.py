@@ -16,6 +16,8 @@ of the operator netlists:
   div       quotient truncated toward zero; a zero divisor, and -2^(k-1)
             divided by -1, are errors here (the divider's bits are
             unspecified there).
+Public constants (m, n, 2 a_num, a_den m) enter as k-bit operands like
+every other value, i.e. modulo 2^k.
 
 Readings (the paper names the equations but not the operator sequence, and
 prints Eq. 12 and Eq. 13 garbled -- the same right-hand side for b' and
@@ -80,13 +82,14 @@ def closed_form(xs, ys, k):
     assert m == len(ys) and m >= 1
     xs = [wrap(x, k) for x in xs]
     ys = [wrap(y, k) for y in ys]
+    mk = wrap(m, k)
     sx = total(xs, k)
-    xbar = div(sx, m, k)
+    xbar = div(sx, mk, k)
     num = total([mul(y, sub(x, xbar, k), k) for x, y in zip(xs, ys)], k)
     sxx = total([mul(x, x, k) for x in xs], k)
-    den = sub(sxx, div(mul(sx, sx, k), m, k), k)
+    den = sub(sxx, div(mul(sx, sx, k), mk, k), k)
     omega = div(num, den, k)
-    b = div(total([sub(y, mul(omega, x, k), k) for x, y in zip(xs, ys)], k), m, k)
+    b = div(total([sub(y, mul(omega, x, k), k) for x, y in zip(xs, ys)], k), mk, k)
     return omega, b
 
 
@@ -111,10 +114,10 @@ def gradient_descent(xs, ys, k, zoom, a_num, a_den, iters, w0=0, b0=0):
 def loss_closed_form(xs, ys, omega, b, k):
     """Eq. 14 for the closed-form model: (sum (y_i - (omega x_i + b))^2) / m."""
     r = [sub(wrap(y, k), add(mul(omega, wrap(x, k), k), b, k), k) for x, y in zip(xs, ys)]
-    return div(total([mul(v, v, k) for v in r], k), len(xs), k)
+    return div(total([mul(v, v, k) for v in r], k), wrap(len(xs), k), k)
 
 
 def loss_gradient_descent(xs, ys, W, B, zoom, k):
     """Eq. 14 for the zoomed model: (sum (y_i - (W x_i + B) / n)^2) / m."""
-    r = [sub(wrap(y, k), div(add(mul(W, wrap(x, k), k), B, k), zoom, k), k) for x, y in zip(xs, ys)]
-    return div(total([mul(v, v, k) for v in r], k), len(xs), k)
+    r = [sub(wrap(y, k), div(add(mul(W, wrap(x, k), k), B, k), wrap(zoom, k), k), k) for x, y in zip(xs, ys)]
+    return div(total([mul(v, v, k) for v in r], k), wrap(len(xs), k), k)

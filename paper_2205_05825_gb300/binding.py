@@ -71,6 +71,7 @@ _SIGS = {
     "mk_load_keys": (ctypes.c_int, [VP, VP, ctypes.c_size_t]),
     "mk_encrypt": (ctypes.c_int, [VP, ctypes.c_uint32, U8P, ctypes.c_size_t, ctypes.c_uint64, U32P]),
     "mk_encrypt_joint": (ctypes.c_int, [VP, U8P, ctypes.c_size_t, ctypes.c_uint64, U32P]),
+    "mk_trivial": (ctypes.c_int, [VP, U8P, ctypes.c_size_t, U32P]),
     "mk_decrypt": (ctypes.c_int, [VP, VP, ctypes.c_size_t, ctypes.c_int, U8P]),
     "mk_phase": (ctypes.c_int, [VP, VP, ctypes.c_size_t, ctypes.c_int, U32P]),
     "mk_gate": (ctypes.c_int, [VP, ctypes.c_int, VP, VP, VP, ctypes.c_size_t]),
@@ -314,6 +315,14 @@ class Context:
         out = np.zeros((len(bits), self.W), np.uint32)
         self._check(self.L.mk_encrypt_joint(self.h, bits.ctypes.data_as(U8P), len(bits), seed,
                                             out.ctypes.data_as(U32P)), "mk_encrypt_joint")
+        return out
+
+    def trivial(self, bits):
+        """Noiseless ciphertexts of public bits (mk_trivial): [count][W] uint32."""
+        bits = np.ascontiguousarray(bits, np.uint8)
+        out = np.zeros((len(bits), self.W), np.uint32)
+        self._check(self.L.mk_trivial(self.h, bits.ctypes.data_as(U8P), len(bits), out.ctypes.data_as(U32P)),
+                    "mk_trivial")
         return out
 
     def _ct_arg(self, ct):

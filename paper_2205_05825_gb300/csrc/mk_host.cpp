@@ -1069,6 +1069,18 @@ int mk_encrypt_joint(mk_ctx *c, const uint8_t *bits, size_t count, uint64_t seed
     return MK_OK;
 }
 
+int mk_trivial(mk_ctx *c, const uint8_t *bits, size_t count, uint32_t *ct) {
+    if (!c) return MK_EINVAL;
+    if (count && (!bits || !ct)) return fail(c, MK_EINVAL, "null pointer");
+    const size_t W = c->W();
+    for (size_t g = 0; g < count; ++g) {
+        uint32_t *row = ct + g * W;
+        std::memset(row, 0, W * 4);
+        row[W - 1] = (bits[g] & 1u) ? (1u << 30) : 0u;
+    }
+    return MK_OK;
+}
+
 static int get_host_rows(mk_ctx *c, const uint32_t *ct, size_t count, int on_device, std::vector<uint32_t> &buf,
                          const uint32_t **rows) {
     if (!on_device) {

@@ -128,6 +128,16 @@ def regression_data(samples=64, features=4, config_id=5):
     return X, w, y
 
 
+def unary_regression_data(m, slope, intercept, x_lo, x_hi, noise, config_id=6):
+    """m points of the unary model (Sec. 3.4): x uniform in [x_lo, x_hi],
+    y = slope x + intercept + noise uniform in [-noise, noise] (the paper's
+    data, linear with random noise, is unpublished)."""
+    r = rng(config_id)
+    x = r.integers(x_lo, x_hi + 1, size=m).astype(np.int64)
+    y = slope * x + intercept + r.integers(-noise, noise + 1, size=m)
+    return [int(v) for v in x], [int(v) for v in y]
+
+
 def gd_request_stream(count, bits=16, config_id=5):
     """`count` single-operation requests (op, a, b) drawn from one integer
     gradient-descent step on regression_data, in the step's own proportions:

@@ -94,3 +94,25 @@ def test_library_keygen_and_encrypt_byte_equal_to_oracle():
     c = o.encrypt(P, keys, 0, bits, 97)
     assert np.array_equal(ctx.decrypt(c), bits)
     assert np.array_equal(ctx.phase(c), o.phase(P, keys, c))
+
+
+def test_trivial_ciphertexts_of_public_bits():
+    """mk_trivial: zero mask, b = m/4, no secret needed; the oracle decrypts
+    it to the bit under the parties' keys with phase exactly m/4, and its
+    gates treat it like any other ciphertext of that bit."""
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.toy_params(2)
+    keys = o.keygen(P, W.CRS_SEED, W.party_seeds(2))
+    ctx = B.Context(P, W.CRS_SEED, device=-1)    # no keys at all
+    bits = np.array([1, 0, 1, 1, 0, 3, 2], np.uint8)  # only the lowest bit counts
+    t = ctx.trivial(bits)
+    assert t.shape == (len(bits), ctx.W) and not t[:, :-1].any()
+    assert np.array_equal(o.phase(P, keys, t), (bits & 1).astype(np.uint32) << 30)
+    assert np.array_equal(o.decrypt(P, keys, t), bits & 1)
+    x = o.encrypt(P, keys, 0, np.array([1, 0, 1, 0], np.uint8), 55)
+    one, zero = ctx.trivial([1, 1, 1, 1]), ctx.trivial([0, 0, 0, 0])
+    g = np.array([0, 0, 4, 4], np.int32)         # AND, AND, XOR, XOR
+    out = o.gates(P, keys, g, x, np.concatenate([one[:2], zero[:2]]))
+    assert list(o.decrypt(P, keys, out)) == [1, 0, 1, 0]
