@@ -187,6 +187,59 @@ def ncu_traffic_per_gate():
         return None
 
 
+# ----------------------------------------------------------------------------- regression application
+def run_regression(dev_index):
+    """Training and evaluation times of the encrypted linear regression at
+    the full parameter set, k = 2: x encrypted by party 0, y by party 1, m = 8
+    points on y = 2x + 1 (Sec. 5.5, Table 8).  Algorithm 7 at 8 bits trains
+    from scratch; Algorithm 8 at 16 bits (zoom 100, learning rate 1/16) times
+    one iteration started at the exact zoomed solution, where both updates
+    are zero.  The exact data make the expected models known without the
+    oracle: (omega, b) = (2, 1), (W, B) unchanged, losses 0.  Wall-clock
+    seconds with the device synchronised on both sides of each phase."""
+    import torch
+
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import regression as G
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.full_params(2)
+    ctx = B.Context(P, W.CRS_SEED, device=dev_index)
+    for i, s_ in enumerate(W.party_seeds(2)):
+        ctx.keygen(i, s_)
+    xs = [-3, -2, -1, 0, 1, 2, 3, 0]          # sum 0: the mean is exact; nothing wraps at 8 bits
+    ys = [2 * x + 1 for x in xs]
+    dev = "cuda:%d" % dev_index
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    dec = lambda ct: int(G.decrypt_integers(ctx, ct)[0])  # noqa: E731
+    cx = G.encrypt_integers(ctx, xs, 8, 0, W.encryption_seed(70, 0), device=dev)
+    cy = G.encrypt_integers(ctx, ys, 8, 1, W.encryption_seed(70, 1), device=dev)
+    (om, b, calls), t_train = timed(lambda: G.closed_form(ctx, 8, cx, cy))
+    (loss, _), t_eval = timed(lambda: G.loss_closed_form(ctx, 8, cx, cy, om, b))
+    cf = {"kbits": 8, "m": len(xs), "train_s": t_train, "eval_s": t_eval, "operator_calls": calls,
+          "model": [dec(om), dec(b)], "loss": dec(loss)}
+    cf["ok"] = cf["model"] == [2, 1] and cf["loss"] == 0
+    n = 100
+    cx = G.encrypt_integers(ctx, xs, 16, 0, W.encryption_seed(71, 0), device=dev)
+    cy = G.encrypt_integers(ctx, ys, 16, 1, W.encryption_seed(71, 1), device=dev)
+    (Wc, Bc, calls), t_iter = timed(lambda: G.gradient_descent(ctx, 16, cx, cy, n, 1, 16, 1, w0=2 * n, b0=n))
+    (loss, _), t_eval = timed(lambda: G.loss_gradient_descent(ctx, 16, cx, cy, Wc, Bc, n))
+    gd = {"kbits": 16, "m": len(xs), "zoom": n, "learning_rate": "1/16", "train_s_per_iter": t_iter,
+          "eval_s": t_eval, "operator_calls": calls, "model": [dec(Wc), dec(Bc)], "loss": dec(loss)}
+    gd["ok"] = gd["model"] == [2 * n, n] and gd["loss"] == 0
+    ctx.close()
+    return {"parties": 2, "closed_form": cf, "gradient_descent": gd,
+            "paper_table8_k2": {"formula_train_s": 227.467, "formula_eval_s": 37.131,
+                                "gd_train_s_per_iter": 1133.33, "gd_eval_s": 190.644,
+                                "note": "Xeon Gold 5220 CPU; the paper does not state its data size"}}
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -371,6 +424,8 @@ def run_ours(args):
                               "active_cmux_steps_per_gate": kk * Pk["n"]})
             ck.close()
 
+    regression = run_regression(dev_index) if args.regression else None
+
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
     mm_per_gate = work_per_cmux(P, args.form) * P["k"] * P["n"]
@@ -426,6 +481,7 @@ def run_ours(args):
                                       "batched_over_plain": value / world / plain_rate},
         "k4": k4,
         "precision_sweep": sweep,
+        "regression": regression,
         "decrypt_ok": bool(ok),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(G + 2 * G * ctx.W * 4),
@@ -520,6 +576,8 @@ def main():
                     help="also time every product form at 2, 4 and 8 parties (8192 joint-key gates each)")
     ap.add_argument("--sweep-forms", default="ntt,ntt2,fft,tc",
                     help="comma-separated product forms the sweep times")
+    ap.add_argument("--regression", action="store_true",
+                    help="also time the encrypted linear regression (Algorithms 7 and 8) at k = 2, full size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
