@@ -65,9 +65,12 @@ class Operators:
         return torch.empty((pairs, rows, self.ctx.W), dtype=torch.int32, device=self.device)
 
     def _prep(self, a, b):
+        """Contiguous, 16-byte aligned operands (the ABI's pointer rule: a
+        row slice of a [count][kbits][W] tensor starts at a multiple of
+        4 kbits W bytes, which need not be one)."""
         if a.shape != b.shape or a.shape[1] != self.k or a.dtype != torch.int32:
             raise ValueError("operands must be int32 [pairs][kbits][W] of one shape")
-        return a.contiguous(), b.contiguous()
+        return tuple(t.clone() if t.data_ptr() % 16 else t for t in (a.contiguous(), b.contiguous()))
 
     def add(self, a, b):
         a, b = self._prep(a, b)

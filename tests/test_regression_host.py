@@ -41,6 +41,7 @@ class PlainContext:
     @staticmethod
     def _bits(t, kbits, pairs):
         assert t.dtype == torch.int32 and t.is_contiguous() and t.numel() == pairs * kbits * W_TEST
+        assert t.data_ptr() % 16 == 0, "the ABI wants 16-byte aligned operands"
         v = t.reshape(pairs, kbits, W_TEST).numpy().view(np.uint32)
         assert not v[..., :-1].any(), "stand-in ciphertexts have zero masks"
         return ((v[..., -1] >> 30) & 1).astype(np.int64)
@@ -125,6 +126,18 @@ def test_gradient_descent_from_given_start_and_wrapping_constants():
     Wc, Bc, _ = G.gradient_descent(ctx, k, _enc(ctx, xs, k), _enc(ctx, ys, k), 300, 1, 100, 2, w0=5, b0=-3)
     assert (int(G.decrypt_integers(ctx, Wc)[0]), int(G.decrypt_integers(ctx, Bc)[0])) == \
         R.gradient_descent(xs, ys, k, 300, 1, 100, 2, w0=5, b0=-3)
+
+
+def test_odd_width_operands_stay_aligned():
+    """At 3 bits a row slice starts at a multiple of 4 * 3 * W bytes, not of
+    16: the module copies such operands before a call."""
+    from paper_2205_05825_gb300 import regression as G
+    ctx = PlainContext()
+    xs, ys = [0, 1, 2], [1, 2, 3]     # the data count is an operand too: m <= 3 at 3 bits
+    k = 3
+    got = G.closed_form(ctx, k, _enc(ctx, xs, k), _enc(ctx, ys, k))
+    ref = R.closed_form(xs, ys, k)
+    assert (int(G.decrypt_integers(ctx, got[0])[0]), int(G.decrypt_integers(ctx, got[1])[0])) == ref
 
 
 def test_integer_bit_codecs():
