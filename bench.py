@@ -479,6 +479,10 @@ def run_ours(args):
         "plain_one_gate_per_launch": {"gates_per_s": plain_rate, "gates": plain_g,
                                       "latency_ms": plain_ms / plain_g,
                                       "batched_over_plain": value / world / plain_rate},
+        "negacyclic_products_per_s": {
+            "value": value * P["k"] * P["n"] * (2 * P["k"] + 4) * P["d"],
+            "per_gate": P["k"] * P["n"] * (2 * P["k"] + 4) * P["d"],
+            "note": "form-independent rate: k n (2k+4) d length-N negacyclic products per gate"},
         "k4": k4,
         "precision_sweep": sweep,
         "regression": regression,
