@@ -22,7 +22,6 @@ import re
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np

@@ -1,6 +1,5 @@
 """The C-ABI library builds, loads without a GPU, and exports every function
 include/*.h declares; host-only contexts work without a device."""
-import ctypes
 import glob
 import os
 import re

@@ -3,7 +3,6 @@ parameter set, two parties: x encrypted by party 0, y by party 1 (each
 participant contributes its own data, Sec. 5.5).  The decrypted model and
 loss equal the regression oracle's integer emulation exactly: every operator
 is an exact circuit, so any gate that decrypted wrongly would show."""
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

@@ -5,7 +5,7 @@ and decrypts to the native two's-complement result."""
 import numpy as np
 import pytest
 
-from conftest import from_dev, oracle_keys, to_dev
+from conftest import from_dev, oracle_keys
 
 pytestmark = pytest.mark.gpu
 

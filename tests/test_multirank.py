@@ -5,7 +5,6 @@ here with two gloo ranks on the CPU."""
 import os
 import sys
 
-import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

@@ -4,7 +4,6 @@ against that copy, which must fail."""
 import os
 import subprocess
 import sys
-import tempfile
 
 import pytest
 
