@@ -115,3 +115,14 @@ def test_trivial_ciphertexts_of_public_bits():
     g = np.array([0, 0, 4, 4], np.int32)         # AND, AND, XOR, XOR
     out = o.gates(P, keys, g, x, np.concatenate([one[:2], zero[:2]]))
     assert list(o.decrypt(P, keys, out)) == [1, 0, 1, 0]
+
+
+def test_trivial_argument_errors(lib):
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    ctx = B.Context(W.toy_params(2), W.CRS_SEED, device=-1)
+    einval = -1
+    assert ctx.L.mk_trivial(ctx.h, None, 3, None) == einval    # null pointers with count > 0
+    assert ctx.L.mk_trivial(ctx.h, None, 0, None) == B.MK_OK   # nothing to do
+    assert ctx.L.mk_trivial(None, None, 0, None) == einval     # no context
+    assert ctx.trivial(np.zeros(0, np.uint8)).shape == (0, ctx.W)
