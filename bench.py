@@ -190,12 +190,14 @@ def ncu_traffic_per_gate():
 def run_regression(dev_index):
     """Training and evaluation times of the encrypted linear regression at
     the full parameter set, k = 2: x encrypted by party 0, y by party 1, m = 8
-    points on y = 2x + 1 (Sec. 5.5, Table 8).  Algorithm 7 at 8 bits trains
-    from scratch; Algorithm 8 at 16 bits (zoom 100, learning rate 1/16) times
-    one iteration started at the exact zoomed solution, where both updates
-    are zero.  The exact data make the expected models known without the
-    oracle: (omega, b) = (2, 1), (W, B) unchanged, losses 0.  Wall-clock
-    seconds with the device synchronised on both sides of each phase."""
+    points on y = 2x + 1 (Sec. 5.5, Table 8), with each operator netlist
+    family (MK_CIRCUIT_ARRAY, MK_CIRCUIT_SHALLOW).  Algorithm 7 at 8 bits
+    trains from scratch; Algorithm 8 at 16 bits (zoom 100, learning rate
+    1/16) times one iteration started at the exact zoomed solution, where
+    both updates are zero.  The exact data make the expected models known
+    without the oracle: (omega, b) = (2, 1), (W, B) unchanged, losses 0.
+    Wall-clock seconds with the device synchronised on both sides of each
+    phase."""
     import torch
 
     from paper_2205_05825_gb300 import binding as B
@@ -217,26 +219,29 @@ def run_regression(dev_index):
         return out, time.perf_counter() - t0
 
     dec = lambda ct: int(G.decrypt_integers(ctx, ct)[0])  # noqa: E731
-    cx = G.encrypt_integers(ctx, xs, 8, 0, W.encryption_seed(70, 0), device=dev)
-    cy = G.encrypt_integers(ctx, ys, 8, 1, W.encryption_seed(70, 1), device=dev)
-    (om, b, calls), t_train = timed(lambda: G.closed_form(ctx, 8, cx, cy))
-    (loss, _), t_eval = timed(lambda: G.loss_closed_form(ctx, 8, cx, cy, om, b))
-    cf = {"kbits": 8, "m": len(xs), "train_s": t_train, "eval_s": t_eval, "operator_calls": calls,
-          "model": [dec(om), dec(b)], "loss": dec(loss)}
-    cf["ok"] = cf["model"] == [2, 1] and cf["loss"] == 0
-    n = 100
-    cx = G.encrypt_integers(ctx, xs, 16, 0, W.encryption_seed(71, 0), device=dev)
-    cy = G.encrypt_integers(ctx, ys, 16, 1, W.encryption_seed(71, 1), device=dev)
-    (Wc, Bc, calls), t_iter = timed(lambda: G.gradient_descent(ctx, 16, cx, cy, n, 1, 16, 1, w0=2 * n, b0=n))
-    (loss, _), t_eval = timed(lambda: G.loss_gradient_descent(ctx, 16, cx, cy, Wc, Bc, n))
-    gd = {"kbits": 16, "m": len(xs), "zoom": n, "learning_rate": "1/16", "train_s_per_iter": t_iter,
-          "eval_s": t_eval, "operator_calls": calls, "model": [dec(Wc), dec(Bc)], "loss": dec(loss)}
-    gd["ok"] = gd["model"] == [2 * n, n] and gd["loss"] == 0
+    out = {"parties": 2, "m": len(xs)}
+    for style in ("array", "shallow"):
+        ctx.set_circuit_style(style)
+        cx = G.encrypt_integers(ctx, xs, 8, 0, W.encryption_seed(70, 0), device=dev)
+        cy = G.encrypt_integers(ctx, ys, 8, 1, W.encryption_seed(70, 1), device=dev)
+        (om, b, calls), t_train = timed(lambda: G.closed_form(ctx, 8, cx, cy))
+        (loss, _), t_eval = timed(lambda: G.loss_closed_form(ctx, 8, cx, cy, om, b))
+        cf = {"kbits": 8, "train_s": t_train, "eval_s": t_eval, "operator_calls": calls,
+              "model": [dec(om), dec(b)], "loss": dec(loss)}
+        cf["ok"] = cf["model"] == [2, 1] and cf["loss"] == 0
+        n = 100
+        cx = G.encrypt_integers(ctx, xs, 16, 0, W.encryption_seed(71, 0), device=dev)
+        cy = G.encrypt_integers(ctx, ys, 16, 1, W.encryption_seed(71, 1), device=dev)
+        (Wc, Bc, calls), t_iter = timed(lambda: G.gradient_descent(ctx, 16, cx, cy, n, 1, 16, 1, w0=2 * n, b0=n))
+        (loss, _), t_eval = timed(lambda: G.loss_gradient_descent(ctx, 16, cx, cy, Wc, Bc, n))
+        gd = {"kbits": 16, "zoom": n, "learning_rate": "1/16", "train_s_per_iter": t_iter, "eval_s": t_eval,
+              "operator_calls": calls, "model": [dec(Wc), dec(Bc)], "loss": dec(loss)}
+        gd["ok"] = gd["model"] == [2 * n, n] and gd["loss"] == 0
+        out[style] = {"closed_form": cf, "gradient_descent": gd}
     ctx.close()
-    return {"parties": 2, "closed_form": cf, "gradient_descent": gd,
-            "paper_table8_k2": {"formula_train_s": 227.467, "formula_eval_s": 37.131,
-                                "gd_train_s_per_iter": 1133.33, "gd_eval_s": 190.644,
-                                "note": "Xeon Gold 5220 CPU; the paper does not state its data size"}}
+    out["paper_table8_k2"] = {"formula_train_s": 227.467, "formula_eval_s": 37.131, "gd_train_s_per_iter": 1133.33,
+                              "gd_eval_s": 190.644, "note": "Xeon Gold 5220 CPU; the paper does not state its data size"}
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm

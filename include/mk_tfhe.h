@@ -134,6 +134,24 @@ int mk_ctx_set_cluster(mk_ctx *ctx, int mode);
  * overhead only, results are identical either way. */
 int mk_ctx_set_graphs(mk_ctx *ctx, int on);
 
+/* Construction family of the operator netlists (same functions, same
+ * quotient and remainder rules).  MK_CIRCUIT_ARRAY (default): the paper's
+ * array constructions (Sec. 4.3-4.5) -- ripple-carry adder and subtractor,
+ * Baugh-Wooley array multiplier with a ripple final addition, CAS-array
+ * divider: O(k) levels per addition, the fewest gates.  MK_CIRCUIT_SHALLOW:
+ * every carry chain replaced by a parallel-prefix (Sklansky) carry network
+ * and the multiplier's partial products reduced by Dadda stages: O(log k)
+ * levels per addition, for 10-25 % more gates in the multiplier and divider
+ * and up to 60 % more in the adders (levels at 8 / 16 bits: add 17 / 33 -> 7 / 9, mul 35 / 75 -> 19 / 26, div 236 / 852 ->
+ * 100 / 223).  Each level is one batched launch whatever its width, so an
+ * evaluation with few pairs per level (latency-bound) runs faster with the
+ * shallow family and one that fills every level (throughput-bound) with the
+ * array family.  Applies to the operator calls and server requests made
+ * after the change; MK_EINVAL for another value.  No paper counterpart. */
+enum { MK_CIRCUIT_ARRAY = 0, MK_CIRCUIT_SHALLOW = 1 };
+int mk_ctx_set_circuit_style(mk_ctx *ctx, int style);
+int mk_ctx_get_circuit_style(const mk_ctx *ctx, int *style);
+
 /* Blind-rotation kernel variants (same results, different register/occupancy
  * trade-offs): 0..MK_NUM_VARIANTS-1.  mk_autotune times every variant on
  * `sample_gates` random ciphertexts on the context's device, keeps the
@@ -276,7 +294,8 @@ int mk_mul_kbit(mk_ctx *ctx, uint32_t kbits, const uint32_t *d_a, const uint32_t
 int mk_div_kbit(mk_ctx *ctx, uint32_t kbits, const uint32_t *d_a, const uint32_t *d_b, uint32_t *d_q,
                 uint32_t *d_r, size_t pairs);
 
-/* The netlist of an operator, for inspection: gate records (output wire of
+/* The netlist of an operator in a construction family (MK_CIRCUIT_*), for
+ * inspection: gate records (output wire of
  * gate g = 2 + 2*kbits + g; wires 0/1 = constants 0/1, then a's bits, then
  * b's bits), outputs encoded as 2*wire + negated, and the number of levels.
  * Any output pointer may be NULL (counts only); caps bound the copies. */
@@ -286,8 +305,9 @@ typedef struct mk_gate_rec {
     uint8_t reserved;
     int32_t a, b;         /* input wires */
 } mk_gate_rec;
-int mk_circuit_netlist(int op, uint32_t kbits, mk_gate_rec *gates, uint32_t gate_cap, uint32_t *n_gates,
-                       int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs, uint32_t *n_levels);
+int mk_circuit_netlist(int op, uint32_t kbits, int style, mk_gate_rec *gates, uint32_t gate_cap,
+                       uint32_t *n_gates, int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs,
+                       uint32_t *n_levels);
 
 /* ---------------------------------------------------------------- serving */
 /* Continuous batching of operator requests from several clients (the paper's

@@ -20,6 +20,7 @@ PRESETS = {"toy": 0, "full": 1, "paper": 2}
 NUM_VARIANTS = 6
 FORMS = {"ntt": 0, "ntt2": 1, "fft": 2, "tc": 3}
 CLUSTER_MODES = {"auto": 0, "off": 1, "on": 2}
+CIRCUIT_STYLES = {"array": 0, "shallow": 1}
 
 U32P = ctypes.POINTER(ctypes.c_uint32)
 U8P = ctypes.POINTER(ctypes.c_uint8)
@@ -88,6 +89,8 @@ _SIGS = {
     "mk_autotune": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]),
     "mk_ctx_set_graphs": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_ctx_set_circuit_style": (ctypes.c_int, [VP, ctypes.c_int]),
+    "mk_ctx_get_circuit_style": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
     "mk_ctx_set_cluster": (ctypes.c_int, [VP, ctypes.c_int]),
     "mk_autotune_form": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
@@ -95,7 +98,7 @@ _SIGS = {
     "mk_sub_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
     "mk_mul_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, ctypes.c_size_t]),
     "mk_div_kbit": (ctypes.c_int, [VP, ctypes.c_uint32, VP, VP, VP, VP, ctypes.c_size_t]),
-    "mk_circuit_netlist": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, VP, ctypes.c_uint32,
+    "mk_circuit_netlist": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.c_int, VP, ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32), VP, ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "mk_server_create": (ctypes.c_int, [VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(VP)]),
@@ -243,6 +246,16 @@ class Context:
     def set_graphs(self, on):
         """Replay each operator's level loop as a captured CUDA graph (default on)."""
         self._check(self.L.mk_ctx_set_graphs(self.h, 1 if on else 0), "mk_ctx_set_graphs")
+
+    def set_circuit_style(self, style):
+        """Netlist family of the operators: "array" (default) or "shallow"."""
+        st = CIRCUIT_STYLES[style] if isinstance(style, str) else int(style)
+        self._check(self.L.mk_ctx_set_circuit_style(self.h, st), "mk_ctx_set_circuit_style")
+
+    def get_circuit_style(self):
+        v = ctypes.c_int()
+        self._check(self.L.mk_ctx_get_circuit_style(self.h, ctypes.byref(v)), "mk_ctx_get_circuit_style")
+        return {b: a for a, b in CIRCUIT_STYLES.items()}[v.value]
 
     def autotune_form(self, sample_gates, forms=("ntt", "ntt2", "tc")):
         """Time each product form (with its best variant); keep the fastest.
@@ -477,19 +490,22 @@ class MkGateRec(ctypes.Structure):
                 ("reserved", ctypes.c_uint8), ("a", ctypes.c_int32), ("b", ctypes.c_int32)]
 
 
-def circuit_netlist(op, kbits):
-    """The library's netlist of an operator as a dict (same shape as the
-    oracle's): ka, kb, gates [(op, a, neg_a, b, neg_b)], outputs [(wire, neg)], levels."""
+def circuit_netlist(op, kbits, style="array"):
+    """The library's netlist of an operator in a construction family as a
+    dict (same shape as the oracle's): ka, kb, gates [(op, a, neg_a, b,
+    neg_b)], outputs [(wire, neg)], levels."""
     L = load()
     ng, no, nl = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
     opi = OPS[op] if isinstance(op, str) else int(op)
-    rc = L.mk_circuit_netlist(opi, kbits, None, 0, ctypes.byref(ng), None, 0, ctypes.byref(no), ctypes.byref(nl))
+    st = CIRCUIT_STYLES[style] if isinstance(style, str) else int(style)
+    rc = L.mk_circuit_netlist(opi, kbits, st, None, 0, ctypes.byref(ng), None, 0, ctypes.byref(no),
+                              ctypes.byref(nl))
     if rc != MK_OK:
         raise MkError("mk_circuit_netlist: %s" % ERRORS.get(rc, rc))
     gates = (MkGateRec * max(ng.value, 1))()
     outs = (ctypes.c_int32 * max(no.value, 1))()
-    rc = L.mk_circuit_netlist(opi, kbits, gates, ng.value, ctypes.byref(ng), outs, no.value, ctypes.byref(no),
-                              ctypes.byref(nl))
+    rc = L.mk_circuit_netlist(opi, kbits, st, gates, ng.value, ctypes.byref(ng), outs, no.value,
+                              ctypes.byref(no), ctypes.byref(nl))
     if rc != MK_OK:
         raise MkError("mk_circuit_netlist: %s" % ERRORS.get(rc, rc))
     return dict(ka=kbits, kb=kbits, gates=[(g.op, g.a, g.neg_a, g.b, g.neg_b) for g in gates[:ng.value]],

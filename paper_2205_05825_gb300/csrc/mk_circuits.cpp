@@ -21,6 +21,22 @@
 //     cout = ((a OR c) AND (b XOR p)) OR (a AND c)), a remainder correction,
 //     compensation back; quotient sign = sign(a) XOR sign(b), remainder with
 //     a's sign (truncating division).
+// Those are the array family (MK_CIRCUIT_ARRAY): ripple carry chains, O(k)
+// levels per addition, the fewest gates.  The shallow family
+// (MK_CIRCUIT_SHALLOW) computes the same functions with every carry chain
+// replaced by a Sklansky parallel-prefix carry network (generate x AND y,
+// propagate x XOR y, the associative combine (G, P) o (G', P') =
+// (G OR (P AND G'), P AND P') over the carry-in and the bits, sums
+// p XOR carry): the adder and subtractor, every row of the non-restoring
+// divider (operand b XOR p, carry-in p), its remainder correction and every
+// compensation increment; the multiplier reduces its Baugh-Wooley partial
+// products by Dadda stages (targets 2, 3, 4, 6, 9, ...) and adds the two
+// remaining rows with the prefix adder.  Gates with a constant input are
+// folded away and gates nobody reads are pruned.  O(log k) levels per
+// addition (the 16-bit divider: 852 -> 223 levels) for 10-25 % more gates
+// in the multiplier and divider and up to 60 % more in the adders: a level
+// is one batched launch whatever its width, so depth is what a narrow,
+// latency-bound evaluation pays for.
 // Levels: a gate's level is 1 + the deepest of its inputs; each level is one
 // batched bootstrap + key-switch launch over all its gates of all pairs.
 #include <algorithm>
@@ -85,6 +101,181 @@ struct Builder {
         return out;
     }
 };
+
+// ---------------------------------------------------------------- shallow family
+// Value of a constant wire reference (0 or 1), else -1.
+int const_value(Wire x) { return x.w <= 1 ? (x.w ^ x.neg) : -1; }
+
+struct ShallowBuilder : Builder {
+    using Builder::Builder;
+    Wire and_(Wire x, Wire y) {
+        const int cx = const_value(x), cy = const_value(y);
+        if (cx == 0 || cy == 0) return kZero;
+        if (cx == 1) return y;
+        if (cy == 1) return x;
+        return gate(OP_AND, x, y);
+    }
+    Wire or_(Wire x, Wire y) {
+        const int cx = const_value(x), cy = const_value(y);
+        if (cx == 1 || cy == 1) return kOne;
+        if (cx == 0) return y;
+        if (cy == 0) return x;
+        return gate(OP_OR, x, y);
+    }
+    Wire xor_(Wire x, Wire y) {
+        const int cx = const_value(x), cy = const_value(y);
+        if (cx >= 0 && cy >= 0) return (cx ^ cy) ? kOne : kZero;
+        if (cx >= 0) return cx ? negw(y) : y;
+        if (cy >= 0) return cy ? negw(x) : x;
+        return gate(OP_XOR, x, y);
+    }
+    // Sum bits of xs + ys + cin (xs.size() bits, carry out dropped).  Element
+    // 0 is (cin, 0), element i >= 1 is (g, p) of bit i - 1; the Sklansky
+    // network leaves in element i the group (G, P) of elements 0..i, whose G
+    // is the carry into bit i.
+    std::vector<Wire> prefix_add(const std::vector<Wire> &xs, const std::vector<Wire> &ys, Wire cin) {
+        const size_t n = xs.size();
+        std::vector<Wire> g, p;
+        for (size_t i = 0; i < n; ++i) {
+            g.push_back(and_(xs[i], ys[i]));
+            p.push_back(xor_(xs[i], ys[i]));
+        }
+        std::vector<Wire> G{cin}, P{kZero};
+        for (size_t i = 0; i + 1 < n; ++i) {
+            G.push_back(g[i]);
+            P.push_back(p[i]);
+        }
+        for (size_t d = 0; ((size_t)1 << d) < n; ++d)
+            for (size_t i = 0; i < n; ++i)
+                if ((i >> d) & 1) {
+                    const size_t j = ((i >> d) << d) - 1;  // top element of the lower half-block
+                    const Wire t = and_(P[i], G[j]);
+                    G[i] = or_(G[i], t);
+                    P[i] = and_(P[i], P[j]);
+                }
+        std::vector<Wire> sum;
+        for (size_t i = 0; i < n; ++i) sum.push_back(xor_(p[i], G[i]));
+        return sum;
+    }
+    // Conditional two's complement: (bits XOR sign) + sign.
+    std::vector<Wire> compensate_prefix(const std::vector<Wire> &bits, Wire sign) {
+        std::vector<Wire> t;
+        for (const Wire &x : bits) t.push_back(xor_(x, sign));
+        return prefix_add(t, std::vector<Wire>(t.size(), kZero), sign);
+    }
+};
+
+// Drop gates whose outputs no output depends on; renumber the rest in
+// construction order.
+Netlist prune(const Netlist &net) {
+    const int32_t base = (int32_t)(2 + net.ka + net.kb);
+    std::vector<char> live(base + net.gates.size(), 0);
+    for (const Wire &o : net.outputs) live[o.w] = 1;
+    for (size_t g = net.gates.size(); g-- > 0;)
+        if (live[base + g]) live[net.gates[g].a] = live[net.gates[g].b] = 1;
+    std::vector<int32_t> id(base + net.gates.size());
+    for (int32_t w = 0; w < base; ++w) id[w] = w;
+    Netlist out;
+    out.ka = net.ka;
+    out.kb = net.kb;
+    for (size_t g = 0; g < net.gates.size(); ++g) {
+        if (!live[base + g]) continue;
+        mk_gate_rec r = net.gates[g];
+        r.a = id[r.a];
+        r.b = id[r.b];
+        id[base + g] = base + (int32_t)out.gates.size();
+        out.gates.push_back(r);
+    }
+    for (const Wire &o : net.outputs) out.outputs.push_back(Wire{id[o.w], o.neg});
+    return out;
+}
+
+Netlist build_shallow_adder(uint32_t k, bool subtract) {
+    ShallowBuilder b(k, k);
+    std::vector<Wire> ys;
+    for (uint32_t i = 0; i < k; ++i) ys.push_back(subtract ? negw(b.B[i]) : b.B[i]);
+    b.net.outputs = b.prefix_add(b.A, ys, subtract ? kOne : kZero);
+    return prune(b.net);
+}
+
+Netlist build_shallow_multiplier(uint32_t k) {
+    ShallowBuilder b(k, k);
+    std::vector<std::vector<Wire>> cols(2 * k);
+    for (uint32_t i = 0; i < k; ++i)
+        for (uint32_t j = 0; j < k; ++j) {
+            const int op = ((i == k - 1) != (j == k - 1)) ? OP_NAND : OP_AND;
+            cols[i + j].push_back(b.gate(op, b.A[j], b.B[i]));
+        }
+    cols[k].push_back(kOne);
+    cols[2 * k - 1].push_back(kOne);
+    // Dadda stages: targets 2, 3, 4, 6, 9, ... below the tallest column
+    size_t tallest = 0;
+    for (const auto &c : cols) tallest = std::max(tallest, c.size());
+    std::vector<size_t> targets{2};
+    while (targets.back() < tallest) targets.push_back(targets.back() * 3 / 2);
+    for (size_t t = targets.size() - 1; t-- > 0;) {
+        const size_t d = targets[t];
+        std::vector<std::vector<Wire>> nw(2 * k), carries(2 * k + 1);
+        for (uint32_t c = 0; c < 2 * k; ++c) {
+            std::vector<Wire> bits = cols[c];
+            size_t pos = 0, h = bits.size() + carries[c].size();
+            while (h > d) {
+                std::pair<Wire, Wire> sc;
+                if (h - d >= 2) {
+                    sc = b.full_adder(bits[pos], bits[pos + 1], bits[pos + 2]);
+                    pos += 3;
+                    h -= 2;
+                } else {
+                    sc = b.half_adder(bits[pos], bits[pos + 1]);
+                    pos += 2;
+                    h -= 1;
+                }
+                nw[c].push_back(sc.first);
+                carries[c + 1].push_back(sc.second);
+            }
+            for (; pos < bits.size(); ++pos) nw[c].push_back(bits[pos]);
+            for (const Wire &w : carries[c]) nw[c].push_back(w);
+        }
+        cols.swap(nw);
+    }
+    std::vector<Wire> xs, ys;
+    for (uint32_t c = 0; c < 2 * k; ++c) {
+        xs.push_back(cols[c].size() >= 1 ? cols[c][0] : kZero);
+        ys.push_back(cols[c].size() >= 2 ? cols[c][1] : kZero);
+    }
+    b.net.outputs = b.prefix_add(xs, ys, kZero);
+    return prune(b.net);
+}
+
+Netlist build_shallow_divider(uint32_t k) {
+    ShallowBuilder b(k, k);
+    const Wire sa = b.A[k - 1], sb = b.B[k - 1];
+    std::vector<Wire> A = b.compensate_prefix(b.A, sa);
+    std::vector<Wire> D = b.compensate_prefix(b.B, sb);
+    D.push_back(kZero);
+    std::vector<Wire> R(k + 1, kZero);
+    Wire p = kOne;
+    std::vector<Wire> q(k);
+    for (int i = (int)k - 1; i >= 0; --i) {
+        std::vector<Wire> sh{A[i]};
+        for (uint32_t j = 0; j < k; ++j) sh.push_back(R[j]);
+        std::vector<Wire> ys;
+        for (uint32_t j = 0; j <= k; ++j) ys.push_back(b.xor_(D[j], p));
+        R = b.prefix_add(sh, ys, p);  // R + (p ? -D : D)
+        q[i] = negw(R[k]);
+        p = q[i];
+    }
+    const Wire s = R[k];
+    std::vector<Wire> m, low(R.begin(), R.begin() + k);
+    for (uint32_t j = 0; j < k; ++j) m.push_back(b.and_(D[j], s));
+    std::vector<Wire> rmag = b.prefix_add(low, m, kZero);
+    const Wire qs = b.xor_(sa, sb);
+    std::vector<Wire> qo = b.compensate_prefix(q, qs);
+    std::vector<Wire> ro = b.compensate_prefix(rmag, sa);
+    b.net.outputs = qo;
+    b.net.outputs.insert(b.net.outputs.end(), ro.begin(), ro.end());
+    return prune(b.net);
+}
 
 Netlist build_adder(uint32_t k, bool subtract) {
     Builder b(k, k);
@@ -202,8 +393,18 @@ Netlist build_divider(uint32_t k) {
 
 }  // namespace
 
-bool build_netlist(int op, uint32_t k, Netlist &out) {
+bool build_netlist(int op, uint32_t k, int style, Netlist &out) {
     if (k < 2 || k > 64) return false;
+    if (style == MK_CIRCUIT_SHALLOW) {
+        switch (op) {
+        case MK_OP_ADD: out = build_shallow_adder(k, false); return true;
+        case MK_OP_SUB: out = build_shallow_adder(k, true); return true;
+        case MK_OP_MUL: out = build_shallow_multiplier(k); return true;
+        case MK_OP_DIV: out = build_shallow_divider(k); return true;
+        default: return false;
+        }
+    }
+    if (style != MK_CIRCUIT_ARRAY) return false;
     switch (op) {
     case MK_OP_ADD: out = build_adder(k, false); return true;
     case MK_OP_SUB: out = build_adder(k, true); return true;

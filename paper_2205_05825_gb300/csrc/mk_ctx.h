@@ -313,12 +313,13 @@ struct mk_ctx {
     // measurement: event pairs around launches, per kernel class
     bool timing = false;
     bool use_graphs = true;               // circuits replay their level loop as a CUDA graph
+    int circuit_style = MK_CIRCUIT_ARRAY;  // netlist family of the operators
     int cluster_mode = MK_CLUSTER_AUTO;   // latency (cluster) kernel for small batches
     uint32_t sm_count = 0;
     cudaStream_t capture_stream = nullptr;  // non-default stream the graphs are captured on
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
     std::vector<cudaEvent_t> ev_pool;
-    std::map<std::tuple<int, uint32_t, uint32_t>, std::unique_ptr<CircuitPlan>> plans;
+    std::map<std::tuple<int, uint32_t, uint32_t, int>, std::unique_ptr<CircuitPlan>> plans;  // op, k, pairs, style
 
     size_t W() const { return (size_t)P.k * P.n + 1; }
     size_t E() const { return (size_t)P.k * P.N + 1; }

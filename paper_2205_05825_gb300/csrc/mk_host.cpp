@@ -349,14 +349,14 @@ int run_gates(mk_ctx *c, DescKind kind, const void *src, int type, const uint32_
 }
 
 int get_plan(mk_ctx *c, int op, uint32_t k, uint32_t pairs, CircuitPlan **out) {
-    auto key = std::make_tuple(op, k, pairs);
+    auto key = std::make_tuple(op, k, pairs, c->circuit_style);
     auto it = c->plans.find(key);
     if (it != c->plans.end()) {
         *out = it->second.get();
         return MK_OK;
     }
     auto plan = std::make_unique<CircuitPlan>();
-    if (!build_netlist(op, k, plan->net)) return fail(c, MK_EINVAL, "unsupported operator or kbits");
+    if (!build_netlist(op, k, c->circuit_style, plan->net)) return fail(c, MK_EINVAL, "unsupported operator or kbits");
     const Netlist &net = plan->net;
     const std::vector<uint32_t> lev = netlist_levels(net);
     const uint32_t L = lev.empty() ? 0 : *std::max_element(lev.begin(), lev.end());
@@ -654,6 +654,19 @@ int mk_ctx_set_cluster(mk_ctx *c, int mode) {
 int mk_ctx_set_graphs(mk_ctx *c, int on) {
     if (!c) return MK_EINVAL;
     c->use_graphs = on != 0;
+    return MK_OK;
+}
+
+int mk_ctx_set_circuit_style(mk_ctx *c, int style) {
+    if (!c) return MK_EINVAL;
+    if (style != MK_CIRCUIT_ARRAY && style != MK_CIRCUIT_SHALLOW) return fail(c, MK_EINVAL, "unknown circuit style");
+    c->circuit_style = style;
+    return MK_OK;
+}
+
+int mk_ctx_get_circuit_style(const mk_ctx *c, int *style) {
+    if (!c || !style) return MK_EINVAL;
+    *style = c->circuit_style;
     return MK_OK;
 }
 
@@ -1185,10 +1198,11 @@ int mk_div_kbit(mk_ctx *c, uint32_t kbits, const uint32_t *d_a, const uint32_t *
     return run_circuit(c, MK_OP_DIV, kbits, d_a, d_b, d_q, pairs, d_r);
 }
 
-int mk_circuit_netlist(int op, uint32_t kbits, mk_gate_rec *gates, uint32_t gate_cap, uint32_t *n_gates,
-                       int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs, uint32_t *n_levels) {
+int mk_circuit_netlist(int op, uint32_t kbits, int style, mk_gate_rec *gates, uint32_t gate_cap,
+                       uint32_t *n_gates, int32_t *outputs, uint32_t out_cap, uint32_t *n_outputs,
+                       uint32_t *n_levels) {
     Netlist net;
-    if (!build_netlist(op, kbits, net)) return MK_EINVAL;
+    if (!build_netlist(op, kbits, style, net)) return MK_EINVAL;
     if (n_gates) *n_gates = (uint32_t)net.gates.size();
     if (n_outputs) *n_outputs = (uint32_t)net.outputs.size();
     if (n_levels) {

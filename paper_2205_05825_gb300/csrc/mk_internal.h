@@ -191,7 +191,7 @@ struct Netlist {
     std::vector<mk_gate_rec> gates;
     std::vector<Wire> outputs;
 };
-bool build_netlist(int op, uint32_t k, Netlist &out);
+bool build_netlist(int op, uint32_t k, int style, Netlist &out);
 mk_lin gate_lin(const mk_gate_rec &g);
 std::vector<uint32_t> netlist_levels(const Netlist &net);
 

@@ -51,7 +51,7 @@ struct mk_server {
     uint32_t *d_pool = nullptr, *d_ext = nullptr;
     GateDesc *d_desc = nullptr, *h_desc = nullptr;
     std::map<uint64_t, uint64_t> free_rows;  // start -> length
-    std::map<std::tuple<int, uint32_t, uint32_t>, std::unique_ptr<ServerPlan>> plans;
+    std::map<std::tuple<int, uint32_t, uint32_t, int>, std::unique_ptr<ServerPlan>> plans;  // op, k, pairs, style
     std::deque<Request *> queued;
     std::vector<Request *> running;
     std::map<uint64_t, std::unique_ptr<Request>> all;
@@ -91,14 +91,14 @@ void free_rows(mk_server *s, uint64_t base, uint64_t n) {
 
 int server_plan(mk_server *s, int op, uint32_t k, uint32_t pairs, ServerPlan **out) {
     mk_ctx *c = s->ctx;
-    auto key = std::make_tuple(op, k, pairs);
+    auto key = std::make_tuple(op, k, pairs, c->circuit_style);
     auto it = s->plans.find(key);
     if (it != s->plans.end()) {
         *out = it->second.get();
         return MK_OK;
     }
     auto plan = std::make_unique<ServerPlan>();
-    if (!build_netlist(op, k, plan->net)) return fail(c, MK_EINVAL, "unsupported operator or kbits");
+    if (!build_netlist(op, k, c->circuit_style, plan->net)) return fail(c, MK_EINVAL, "unsupported operator or kbits");
     const Netlist &net = plan->net;
     const std::vector<uint32_t> lev = netlist_levels(net);
     const uint32_t L = lev.empty() ? 0 : *std::max_element(lev.begin(), lev.end());

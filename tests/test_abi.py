@@ -126,3 +126,17 @@ def test_trivial_argument_errors(lib):
     assert ctx.L.mk_trivial(ctx.h, None, 0, None) == B.MK_OK   # nothing to do
     assert ctx.L.mk_trivial(None, None, 0, None) == einval     # no context
     assert ctx.trivial(np.zeros(0, np.uint8)).shape == (0, ctx.W)
+
+
+def test_circuit_style_setting(lib):
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    ctx = B.Context(W.toy_params(2), W.CRS_SEED, device=-1)
+    assert ctx.get_circuit_style() == "array"
+    ctx.set_circuit_style("shallow")
+    assert ctx.get_circuit_style() == "shallow"
+    with pytest.raises(B.MkError):
+        ctx.set_circuit_style(7)
+    assert ctx.get_circuit_style() == "shallow"
+    with pytest.raises(B.MkError):
+        B.circuit_netlist("add", 8, 5)

@@ -1,9 +1,12 @@
 """k-bit two's-complement operators (Sec. 3.3, Sec. 4.3-4.5, Alg. 3-6).
 
-Pins: the oracle's netlists against native integer arithmetic (exhaustive
-for 2..5-bit operands, random pairs at 8 and 16 bits); the library's netlists
-are structurally identical to the oracle's; the adder's gate count equals
-Table 3; the oracle's encrypted evaluation decrypts to the native result."""
+Pins: the oracle's netlists of both construction families (array, shallow)
+against native integer arithmetic (exhaustive for 2..5-bit operands, random
+pairs at 8 and 16 bits, edge operands at every width up to 64 for the
+shallow family); the library's netlists are structurally identical to the
+oracle's; the adder's gate count equals Table 3; the shallow family is
+shallower; the oracle's encrypted evaluation decrypts to the native
+result."""
 import os
 
 import numpy as np
@@ -51,14 +54,15 @@ def operands(k, count=2000):
     return W.random_operands(k, count)
 
 
+@pytest.mark.parametrize("style", ["array", "shallow"])
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 8, 16])
-def test_netlist_plaintext_against_native(op, k):
+def test_netlist_plaintext_against_native(op, k, style):
     a, b = operands(k)
     if op == "div":
         ok = valid_div(a, b, k)
         a, b = a[ok], b[ok]
-    net = C.build(op, k)
+    net = C.build(op, k, style)
     got = decode(op, C.eval_plain(net, W.int_to_bits(a, k), W.int_to_bits(b, k)), k)
     exp = expected(op, a, b, k)
     if op == "div":
@@ -67,14 +71,60 @@ def test_netlist_plaintext_against_native(op, k):
         assert np.array_equal(got, exp)
 
 
+def _value(row):
+    k = len(row)
+    v = sum(int(x) << i for i, x in enumerate(row))
+    return v - (1 << k) if row[-1] else v
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_shallow_netlists_at_every_width(op):
+    """Widths 6..64 (beyond int64 products): random and extreme operands,
+    checked with Python integers."""
+    rng = np.random.default_rng(7)
+    for k in range(6, 65):
+        lo, hi = -(1 << (k - 1)), (1 << (k - 1)) - 1
+        a = [lo, lo, hi, -1, 0] + [int(v) for v in rng.integers(-(1 << 62), 1 << 62, size=6) >> max(0, 63 - k)]
+        b = [1, hi, lo, -1, 5] + [int(v) | 1 for v in rng.integers(-(1 << 62), 1 << 62, size=6) >> max(0, 63 - k)]
+        A = np.array([[(x >> i) & 1 for i in range(k)] for x in a])
+        B_ = np.array([[(y >> i) & 1 for i in range(k)] for y in b])
+        out = C.eval_plain(C.build(op, k, "shallow"), A, B_)
+        for row, x, y in zip(out, a, b):
+            if op == "add":
+                assert _value(row) == ((x + y - lo) % (1 << k)) + lo
+            elif op == "sub":
+                assert _value(row) == ((x - y - lo) % (1 << k)) + lo
+            elif op == "mul":
+                assert _value(row) == x * y
+            elif y != 0 and not (x == lo and y == -1):
+                q = abs(x) // abs(y)
+                q = -q if (x < 0) != (y < 0) else q
+                assert (_value(row[:k]), _value(row[k:])) == (q, x - q * y)
+
+
+def test_shallow_family_is_shallower():
+    """Levels (one batched launch each) of the two families, and the gate
+    overhead of the shallow one."""
+    depth = {}
+    for op in ("add", "sub", "mul", "div"):
+        for k in (8, 16):
+            arr, sh = C.build(op, k, "array"), C.build(op, k, "shallow")
+            depth[(op, k)] = (max(C.levels(arr)), max(C.levels(sh)))
+            assert depth[(op, k)][1] < depth[(op, k)][0]
+            assert len(sh["gates"]) <= 1.6 * len(arr["gates"])
+    assert depth[("add", 16)] == (33, 9) and depth[("mul", 16)] == (75, 26)
+    assert depth[("div", 8)] == (236, 100) and depth[("div", 16)] == (852, 223)
+
+
+@pytest.mark.parametrize("style", ["array", "shallow"])
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8, 12, 16])
-def test_library_netlist_equals_oracle_netlist(op, k):
+def test_library_netlist_equals_oracle_netlist(op, k, style):
     from paper_2205_05825_gb300 import binding as B
     from paper_2205_05825_gb300 import build
     build.build()
-    lib = B.circuit_netlist(op, k)
-    ref = C.build(op, k)
+    lib = B.circuit_netlist(op, k, style)
+    ref = C.build(op, k, style)
     assert lib["gates"] == [tuple(g) for g in ref["gates"]]
     assert lib["outputs"] == [tuple(o) for o in ref["outputs"]]
     assert lib["levels"] == max(C.levels(ref))
