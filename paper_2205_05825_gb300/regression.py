@@ -33,7 +33,9 @@ and Eq. 13 garbled; the sequences below are the readings:
 Independent operator instances of one step share a call (more operand
 pairs, the same number of netlist levels): the operators are evaluated
 level by level over all their pairs, so a call costs its netlist depth in
-launches whatever its width.
+launches whatever its width.  For the same reason the calls here, with one
+to a few pairs, suit the context's shallow netlist family
+(ctx.set_circuit_style("shallow")); the results do not depend on it.
 """
 import numpy as np
 import torch
