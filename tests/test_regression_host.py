@@ -17,13 +17,14 @@ W_TEST = 5  # stand-in ciphertext width (mask of 4 words + b)
 
 
 class PlainContext:
-    def __init__(self):
+    def __init__(self, style="array"):
         self.W = W_TEST
+        self.style = style
         self.nets = {}
 
     def _net(self, op, k):
         if (op, k) not in self.nets:
-            self.nets[(op, k)] = C.build(op, k)
+            self.nets[(op, k)] = C.build(op, k, self.style)
         return self.nets[(op, k)]
 
     def trivial(self, bits):
@@ -156,3 +157,18 @@ def test_bad_shapes_are_refused():
         G.closed_form(ctx, 8, x, _enc(ctx, [1, 2, 3], 8))
     with pytest.raises(ValueError):
         G.gradient_descent(ctx, 16, x, x, 10, 1, 10, 1)
+
+
+def test_both_netlist_families_give_the_same_models():
+    """The application on the shallow netlists equals the oracle as on the
+    array ones (the families compute the same functions)."""
+    from paper_2205_05825_gb300 import regression as G
+    from paper_2205_05825_gb300 import workloads as W
+    xs, ys = W.unary_regression_data(6, 2, 1, -3, 4, 1, config_id=61)
+    for style in ("array", "shallow"):
+        ctx = PlainContext(style)
+        om, b, _ = G.closed_form(ctx, 8, _enc(ctx, xs, 8), _enc(ctx, ys, 8))
+        assert (int(G.decrypt_integers(ctx, om)[0]), int(G.decrypt_integers(ctx, b)[0])) == R.closed_form(xs, ys, 8)
+        Wc, Bc, _ = G.gradient_descent(ctx, 16, _enc(ctx, xs, 16), _enc(ctx, ys, 16), 100, 1, 16, 2)
+        assert (int(G.decrypt_integers(ctx, Wc)[0]), int(G.decrypt_integers(ctx, Bc)[0])) == \
+            R.gradient_descent(xs, ys, 16, 100, 1, 16, 2)
