@@ -90,6 +90,8 @@ def main():
     ap.add_argument("--toy", action="store_true")
     ap.add_argument("--cluster", default="auto", choices=["auto", "on", "off"],
                     help="latency (cluster) blind rotation for small waves")
+    ap.add_argument("--circuit-style", default="array", choices=["array", "shallow"],
+                    help="operator netlist family: fewest gates (array) or fewest levels (shallow)")
     args = ap.parse_args()
     B.load(build_if_missing=True)
     P = W.toy_params(args.parties) if args.toy else W.full_params(args.parties)
@@ -98,6 +100,7 @@ def main():
         ctx.keygen(i, s)
     ctx.autotune(1024)
     ctx.set_cluster(args.cluster)
+    ctx.set_circuit_style(args.circuit_style)
     server = B.Server(ctx, wave_gates=args.wave_gates, pool_rows=1 << 20)
     client = Client(ctx, args.bits)
     stream = W.gd_request_stream(max(args.capacity_requests, args.requests), bits=args.bits)
