@@ -118,7 +118,7 @@ def test_shallow_family_is_shallower():
 
 @pytest.mark.parametrize("style", ["array", "shallow"])
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
-@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8, 12, 16])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8, 12, 16, 17, 31, 33, 64])
 def test_library_netlist_equals_oracle_netlist(op, k, style):
     from paper_2205_05825_gb300 import binding as B
     from paper_2205_05825_gb300 import build
