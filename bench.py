@@ -146,7 +146,7 @@ def work_per_cmux(P, form="ntt"):
 UNITS_PER_BUTTERFLY = {"ntt": 1, "ntt2": 1, "fft": 8, "tc": 2}
 UNIT_NAME = {"ntt": "G modmul/s", "ntt2": "G modmul/s", "fft": "G FP64 instr/s", "tc": "TFLOP/s"}
 FORM_DESC = {"ntt": "ntt64 (exact, Goldilocks prime)",
-             "ntt2": "ntt2x30 (exact, two 30-bit primes + CRT)",
+             "ntt2": "ntt2x28 (exact, two 28-bit primes + CRT)",
              "fft": "fft64 (FP64, rounded; approximate)",
              "tc": "tc-bf16 (exact, tensor-core Toeplitz products of key byte planes)"}
 
@@ -458,7 +458,7 @@ def run_ours(args):
                     "peak_source": ("measured: register-resident butterfly loop of the same arithmetic on every "
                                     "SM (mk_measure_butterfly_rate, %s)"
                                     % {"ntt": "Goldilocks 64-bit, one modmul per butterfly",
-                                       "ntt2": "Harvey/Shoup mod a 30-bit prime, one modmul per butterfly",
+                                       "ntt2": "Harvey/Shoup mod a 28-bit prime, one modmul per butterfly",
                                        "fft": "complex FP64, 8 FP64 instructions per butterfly"}[args.form]),
                     "br_share_of_step": br_ms / total_ms if total_ms else None}
 

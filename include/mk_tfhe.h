@@ -94,7 +94,7 @@ int mk_ctx_get_params(const mk_ctx *ctx, mk_params *out);
  * on the next gate call.  Default: MK_FORM_NTT2. */
 enum {
     MK_FORM_NTT = 0,  /* NTT over the prime 2^64 - 2^32 + 1 */
-    MK_FORM_NTT2 = 1, /* NTTs over the primes 0x3fff4001 and 0x3ffee001, CRT */
+    MK_FORM_NTT2 = 1, /* NTTs over the primes 0x0fff0001 and 0x0ffee001, CRT */
     MK_FORM_FFT = 2,  /* FP64 FFT of N/2 folded complex points */
     MK_FORM_TC = 3    /* tensor cores: Toeplitz products of key byte planes and
                          gadget digits, bf16 operands, fp32 sums (exact) */
@@ -153,14 +153,20 @@ int mk_ctx_set_circuit_style(mk_ctx *ctx, int style);
 int mk_ctx_get_circuit_style(const mk_ctx *ctx, int *style);
 
 /* Blind-rotation kernel variants (same results, different register/occupancy
- * trade-offs): 0..MK_NUM_VARIANTS-1.  mk_autotune times every variant on
+ * trade-offs): 0..MK_NUM_VARIANTS-1.  0-5: one CTA per gate, with different
+ * digit polynomials per forward pass, register caps, twiddle placement and
+ * elements per thread; 6: several gates per CTA sharing each CMux step's
+ * bootstrapping-key entry, bulk-copied once into shared memory; 7, 8
+ * (MK_FORM_NTT2): the two primes' transforms on separate warps, recombined
+ * by CRT through shared memory (MK_FORM_NTT runs variant 2's kernel for 7
+ * and 8).  mk_autotune times every variant on
  * `sample_gates` random ciphertexts on the context's device, keeps the
  * fastest for the context and stores it in *best (and, if ms_out is not
  * NULL, each variant's milliseconds in ms_out[0..MK_NUM_VARIANTS-1]).  It
  * synchronises the stream.  MK_FORM_FFT and MK_FORM_TC have one kernel for
  * every variant number: there it times nothing, reports 0 ms and keeps the
  * variant.  No paper counterpart: a tuning aid. */
-#define MK_NUM_VARIANTS 6
+#define MK_NUM_VARIANTS 9
 int mk_ctx_set_variant(mk_ctx *ctx, int variant);
 int mk_ctx_get_variant(const mk_ctx *ctx, int *variant);
 int mk_autotune(mk_ctx *ctx, uint32_t sample_gates, int *best, float *ms_out);
@@ -399,7 +405,7 @@ int mk_timing_read(mk_ctx *ctx, int kernel, double *ms_total, uint64_t *launches
  * butterflies on every SM of `device`; *per_s receives butterflies per
  * second.  form = MK_FORM_NTT: Goldilocks butterflies (one 64-bit modular
  * multiply, add and subtract); MK_FORM_NTT2: Harvey butterflies modulo a
- * 30-bit prime (one Shoup multiply, one conditional subtraction, add, sub);
+ * 28-bit prime (one Shoup multiply, one conditional subtraction, add, sub);
  * MK_FORM_FFT: complex FP64 butterflies (one complex multiply, two complex
  * additions); MK_FORM_TC: multiply-accumulates per second of independent
  * warp-level bf16 m16n8k16 MMAs (the instruction of the tensor form).

@@ -17,7 +17,7 @@ ERRORS = {-1: "MK_EINVAL", -2: "MK_ENOMEM", -3: "MK_EPARAMS", -4: "MK_ETIMEOUT",
           -6: "MK_ESTATE", -7: "MK_EFORMAT"}
 GATES = {"AND": 0, "OR": 1, "NAND": 2, "NOR": 3, "XOR": 4, "XNOR": 5}
 PRESETS = {"toy": 0, "full": 1, "paper": 2}
-NUM_VARIANTS = 6
+NUM_VARIANTS = 9
 FORMS = {"ntt": 0, "ntt2": 1, "fft": 2, "tc": 3}
 CLUSTER_MODES = {"auto": 0, "off": 1, "on": 2}
 CIRCUIT_STYLES = {"array": 0, "shallow": 1}
@@ -458,7 +458,7 @@ def lin_records(types):
 
 def measure_butterfly_rate(device=0, stream=None, iters=4096, form="ntt"):
     """Butterflies per second on every SM: Goldilocks (form "ntt"), Harvey
-    butterflies modulo a 30-bit prime ("ntt2"), complex FP64 butterflies
+    butterflies modulo a 28-bit prime ("ntt2"), complex FP64 butterflies
     ("fft") -- the pipe ceiling of each form; for "tc", multiply-accumulates
     per second of bf16 m16n8k16 MMAs."""
     r = ctypes.c_double()

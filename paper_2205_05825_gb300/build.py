@@ -22,13 +22,14 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mk_kernels.cu", "mk_noalloc.cu", "mk_tensor.cu", "mk_tensor_tc05.cu"]
 # mk_br.cu is compiled once per (log2 N, blind-rotation variant).
 BR_SOURCE = "mk_br.cu"
-BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(6)] + \
+BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(9)] + \
     [(logn, 2, 0) for logn in (8, 10)]
 # mk_brc.cu (the cluster kernel) is compiled once per (log2 N, field).
 BRC_SOURCE = "mk_brc.cu"
 BRC_INSTANCES = [(logn, f) for logn in (8, 10) for f in (0, 1)]
 CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp", "mk_server.cpp"]
 HEADERS = ["mk_internal.h", "mk_ctx.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", "mk_bootstrap_cluster.cuh",
+           "mk_bootstrap_staged.cuh", "mk_bootstrap_split.cuh",
            BR_SOURCE, BRC_SOURCE]
 
 

@@ -20,12 +20,15 @@
 //
 // Two exact fields implement the transform (template parameter F):
 //   FieldGold: the prime p = 2^64 - 2^32 + 1, one 64-bit residue per element;
-//   FieldDual: two 30-bit primes p1, p2 (p1 p2 > 2^59 > 2 |sum|), a pair of
-//     32-bit residues per element, recombined by CRT after the inverse
-//     transform.  Harvey's lazy butterflies (values kept in [0, 4p)) with
-//     Shoup's precomputed quotients for the twiddles (two dependent
-//     multiplies); keys in Montgomery form (times 2^32 mod p), so a pointwise
-//     product is three multiply-adds without a second table.
+//   FieldDual: two 28-bit primes p1, p2 (p1 p2 > 2^55.9 > 2 |sum|, keys as
+//     signed 32-bit values), a pair of 32-bit residues per element,
+//     recombined by CRT after the inverse transform.  Harvey's lazy
+//     butterflies (values kept in [0, 4p)) with Shoup's precomputed quotients
+//     for the twiddles (two dependent multiplies); keys in Montgomery form
+//     (times 2^32 mod p), so a pointwise product is three multiply-adds
+//     without a second table.  (Letting forward values grow for six stages
+//     before one reduction -- fewer instructions on paper -- measured slower
+//     and with more executed instructions on GB300.)
 // Both give the exact integer product sums, hence identical ciphertexts.
 //
 // Paper steps (arXiv 2205.05825): gate linear part (Sec. 4.1, Eq. 6-11,
@@ -34,6 +37,8 @@
 // u_j = g^-1(c_j); v = -<u_0, a> + sum_{j>=1} <u_j, pk_j>; w = g^-1(v);
 // c'_j = <u_j, d>; c'_0 += <w, f0>; c'_i += <w, f1>.
 #pragma once
+#include <type_traits>
+
 #include "mk_internal.h"
 
 namespace mk {
@@ -152,7 +157,8 @@ __device__ __forceinline__ uint32_t shoup(uint32_t x, uint32_t w, uint32_t wp, u
 
 __device__ __forceinline__ uint32_t red2p(uint32_t x, uint32_t twop) { return min(x, x - twop); }
 
-// Montgomery: x * k * 2^-32 mod p in [0, 2p) for x < 4p, k < p.
+// Montgomery: x * k * 2^-32 mod p in [0, 2p) for any x < 2^32 and k < p
+// ((x k + m p) / 2^32 < k + p).
 __device__ __forceinline__ uint32_t montmul(uint32_t x, uint32_t k, uint32_t p, uint32_t pinv) {
     const uint64_t t = (uint64_t)x * k;
     const uint32_t m = (uint32_t)t * pinv;
@@ -164,8 +170,9 @@ struct FieldDual {
     using Tw = uint4;  // (w1, w2, w1', w2'): twiddles with Shoup companions
     static constexpr int kForm = 1;
     __device__ static __forceinline__ E zero() { return make_uint2(0, 0); }
+    // u + p in [p - 2^9, p + 2^9) within [0, 2p): no branch on the sign.
     __device__ static __forceinline__ E from_digit(int32_t u) {
-        return u >= 0 ? make_uint2((uint32_t)u, (uint32_t)u) : make_uint2(P1 + u, P2 + u);
+        return make_uint2(P1 + (uint32_t)u, P2 + (uint32_t)u);
     }
     // Harvey: inputs in [0, 4p), outputs in [0, 4p).
     __device__ static __forceinline__ void fwd(E &X, E &Y, const Tw &S) {
@@ -180,7 +187,7 @@ struct FieldDual {
         X = make_uint2(red2p(u1 + v1, TWO_P1), red2p(u2 + v2, TWO_P2));
         Y = make_uint2(shoup(u1 - v1 + TWO_P1, S.x, S.z, P1), shoup(u2 - v2 + TWO_P2, S.y, S.w, P2));
     }
-    // acc in [0, 2p), x in [0, 4p), k in Montgomery form.
+    // acc in [0, 2p), any x, k in Montgomery form.
     __device__ static __forceinline__ void mac(E &acc, const E &x, const E &k) {
         acc.x = red2p(acc.x + montmul(x.x, k.x, P1, PINV1), TWO_P1);
         acc.y = red2p(acc.y + montmul(x.y, k.y, P2, PINV2), TWO_P2);
@@ -195,16 +202,62 @@ struct FieldDual {
     }
 };
 
-// EPT consecutive 8-byte elements (EPT even) through the read-only cache.
-template <int EPT, class E>
-__device__ __forceinline__ void load_ept(const E *__restrict__ src, E (&v)[EPT]) {
-    static_assert(sizeof(E) == 8 && EPT % 2 == 0, "8-byte elements, an even count");
-    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+// Layouts of an NTT-domain key polynomial (transform order), chosen so that
+// a thread holding EPT = 8 consecutive elements reads them with 16-byte loads
+// that are contiguous across the warp: coalesced in global memory and free of
+// bank conflicts in shared memory.
+//  * 8-byte elements (MK_FORM_NTT): the 16-byte unit u (elements 2u, 2u + 1)
+//    is stored at unit position (u % 4) * (N / 8) + u / 4, so unit q of
+//    thread t's four is at q * (N / 8) + t.
+//  * two residues (MK_FORM_NTT2): two planes of N words (residues mod p1,
+//    then mod p2); in each plane the 16-byte unit u (elements 4u .. 4u + 3)
+//    is stored at (u % 2) * (N / 8) + u / 2, so unit r of thread t's two is
+//    at r * (N / 8) + t.  A kernel that works on one prime reads one plane.
+template <int LOGN>
+__host__ __device__ __forceinline__ int key_unit_pos(int u) {
+    return (u & 3) * ((1 << LOGN) / 8) + (u >> 2);
+}
+template <int LOGN>
+__host__ __device__ __forceinline__ int plane_unit_pos(int u) {
+    return (u & 1) * ((1 << LOGN) / 8) + (u >> 1);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ uint4 load16(const uint4 *p) {
+    if constexpr (SMEM) return *p;
+    else return __ldg(p);
+}
+
+// The EPT elements of thread tid (transform positions EPT*tid ..) of one key
+// polynomial; global memory through the read-only cache, or shared memory.
+template <int LOGN, int EPT, bool SMEM = false, class E>
+__device__ __forceinline__ void load_ept(const E *__restrict__ poly, int tid, E (&v)[EPT]) {
+    static_assert(sizeof(E) == 8 && EPT % 4 == 0, "8-byte elements, a multiple of four");
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(poly);
+    if constexpr (std::is_same<E, uint2>::value) {
+        constexpr int PU = (1 << LOGN) / 4;  // 16-byte units per plane
 #pragma unroll
-    for (int q = 0; q < EPT / 2; ++q) {
-        const uint4 t = __ldg(s4 + q);
-        reinterpret_cast<uint4 *>(v)[q] = t;
+        for (int r = 0; r < EPT / 4; ++r) {
+            const int pos = plane_unit_pos<LOGN>(tid * (EPT / 4) + r);
+            const uint4 a = load16<SMEM>(s4 + pos), b = load16<SMEM>(s4 + PU + pos);
+            v[4 * r] = make_uint2(a.x, b.x);
+            v[4 * r + 1] = make_uint2(a.y, b.y);
+            v[4 * r + 2] = make_uint2(a.z, b.z);
+            v[4 * r + 3] = make_uint2(a.w, b.w);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < EPT / 2; ++q) {
+            const uint4 t = load16<SMEM>(s4 + key_unit_pos<LOGN>(tid * (EPT / 2) + q));
+            reinterpret_cast<uint4 *>(v)[q] = t;
+        }
     }
+}
+
+// Named barrier of the bar_id-th thread group of nthreads (bar_id 0: the CTA).
+__device__ __forceinline__ void group_sync(int bar_id, int nthreads) {
+    if (bar_id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;\n" ::"r"(bar_id), "r"(nthreads) : "memory");
 }
 
 // ------------------------------------------------------------ negacyclic NTT
@@ -282,30 +335,32 @@ struct Ntt {
         }
     }
 
+    // bar_id: the named barrier of the T threads that own the polynomials
+    // (0: the whole CTA is those threads).
     template <int NP>
-    __device__ static __forceinline__ void exchange(E (&x)[NP][EPT], int tid, E *buf, int LOf, int LOt) {
+    __device__ static __forceinline__ void exchange(E (&x)[NP][EPT], int tid, E *buf, int LOf, int LOt, int bar_id) {
         const int bf = jbase<SB>(tid, LOf);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
             for (int c = 0; c < EPT; ++c) buf[p * PN + pidx(bf | (c << LOf))] = x[p][c];
-        __syncthreads();
+        group_sync(bar_id, T);
         const int bt = jbase<SB>(tid, LOt);
 #pragma unroll
         for (int p = 0; p < NP; ++p)
 #pragma unroll
             for (int c = 0; c < EPT; ++c) x[p][c] = buf[p * PN + pidx(bt | (c << LOt))];
-        __syncthreads();
+        group_sync(bar_id, T);
     }
 
     // natural (layout logN-SB) -> bit-reversed (layout 0)
     template <int NP>
-    __device__ static __forceinline__ void forward(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf) {
+    __device__ static __forceinline__ void forward(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf, int bar_id = 0) {
         int prev = LOGN - SB;
 #pragma unroll 1
         for (int hi = LOGN - 1; hi >= 0; hi -= SB) {
             const int LO = hi >= SB - 1 ? hi - (SB - 1) : 0;
-            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO);
+            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO, bar_id);
             const int jb = jbase<SB>(tid, LO);
             if constexpr (SB == 3) {
                 if (hi - LO == 2) fwd_stage<NP, 4>(x, jb, LO, LO + 2, tw);
@@ -318,13 +373,13 @@ struct Ntt {
 
     // bit-reversed (layout 0) -> natural (layout logN-SB), without 1/N
     template <int NP>
-    __device__ static __forceinline__ void inverse(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf) {
+    __device__ static __forceinline__ void inverse(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf, int bar_id = 0) {
         int prev = 0;
 #pragma unroll 1
         for (int lo = 0; lo < LOGN; lo += SB) {
             const int hi = (lo + SB - 1 < LOGN - 1) ? lo + SB - 1 : LOGN - 1;
             const int LO = (lo < LOGN - SB) ? lo : LOGN - SB;
-            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO);
+            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO, bar_id);
             const int jb = jbase<SB>(tid, LO);
             if (lo == LO) inv_stage<NP, 1>(x, jb, LO, LO, tw);
             if (lo <= LO + 1 && hi >= LO + 1) inv_stage<NP, 2>(x, jb, LO, LO + 1, tw);
@@ -382,20 +437,77 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
     return L;
 }
 
-// A += x * key over EPT elements; key words at key + EPT*tid (layout 0).
-template <class F, int EPT>
+// A += x * key over the EPT elements of thread tid (transform layout 0) of
+// the key polynomial `key` (unit-interleaved, in global or shared memory).
+template <class F, int LOGN, int EPT, bool SMEM = false>
 __device__ __forceinline__ void mac_ept(typename F::E (&A)[EPT], const typename F::E (&x)[EPT],
                                         const typename F::E *__restrict__ key, int tid) {
     typename F::E kv[EPT];
-    load_ept<EPT>(key + tid * EPT, kv);
+    load_ept<LOGN, EPT, SMEM>(key, tid, kv);
 #pragma unroll
     for (int c = 0; c < EPT; ++c) F::mac(A[c], x[c], kv[c]);
 }
 
-template <class F>
+template <class F, int LOGN>
 __device__ __forceinline__ void mac8(typename F::E (&A)[8], const typename F::E (&x)[8],
                                      const typename F::E *__restrict__ key, int tid) {
-    mac_ept<F, 8>(A, x, key, tid);
+    mac_ept<F, LOGN, 8>(A, x, key, tid);
+}
+
+// Montgomery reduction of t < 2^32 p: t * 2^-32 mod p in [0, 2p).
+__device__ __forceinline__ uint32_t redc(uint64_t t, uint32_t p, uint32_t pinv) {
+    const uint32_t m = (uint32_t)t * pinv;
+    return (uint32_t)((t + (uint64_t)m * p) >> 32);
+}
+
+// Two-prime form, three digit polynomials at once (EPT = 8):
+//   A += x[0] * key[0] + x[1] * key[1] + x[2] * key[2]
+// with key[l] = key + l N.  The three products of an element are summed in
+// 64 bits and reduced once: each is below 4p * p (x from the forward
+// transform, below 4p; key words below p), so the sum is below 12 p^2 <
+// 2^32 p for p < 2^28 and redc returns it in [0, 2p).  One multiply-add per
+// product instead of a Montgomery reduction per product.
+template <int LOGN, bool SMEM = false>
+__device__ __forceinline__ void mac3_dual(uint2 (&A)[8], const uint2 (&x)[3][8], const uint2 *__restrict__ key,
+                                          int tid) {
+    constexpr int N = 1 << LOGN, PU = N / 4;  // 16-byte units per plane
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(key);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pos = plane_unit_pos<LOGN>(2 * tid + r);
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+            const uint32_t p = pl ? P2 : P1, pinv = pl ? PINV2 : PINV1, twop = pl ? TWO_P2 : TWO_P1;
+            uint4 kw[3];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) kw[l] = load16<SMEM>(k4 + (size_t)l * 2 * PU + pl * PU + pos);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = 4 * r + e;
+                uint64_t t = 0;
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const uint32_t kv = e == 0 ? kw[l].x : (e == 1 ? kw[l].y : (e == 2 ? kw[l].z : kw[l].w));
+                    const uint32_t xv = pl ? x[l][c].y : x[l][c].x;
+                    t += (uint64_t)xv * kv;
+                }
+                uint32_t &a = pl ? A[c].y : A[c].x;
+                a = red2p(a + redc(t, p, pinv), twop);
+            }
+        }
+    }
+}
+
+// A += sum_l x[l] * key[l] over the NPF digit polynomials of a forward pass.
+template <class F, int LOGN, int EPT, int NPF, bool SMEM = false>
+__device__ __forceinline__ void mac_npf(typename F::E (&A)[EPT], const typename F::E (&x)[NPF][EPT],
+                                        const typename F::E *__restrict__ key, int tid) {
+    if constexpr (NPF == 3 && EPT == 8 && std::is_same<typename F::E, uint2>::value) {
+        mac3_dual<LOGN, SMEM>(A, x, key, tid);
+    } else {
+#pragma unroll
+        for (int p = 0; p < NPF; ++p) mac_ept<F, LOGN, EPT, SMEM>(A, x[p], key + (size_t)p * (1 << LOGN), tid);
+    }
 }
 
 // One CMux step for party i (1..k) at rotation e:
@@ -447,20 +559,16 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
                     for (int p = 0; p < NPF; ++p) x[p][c] = F::from_digit(G.digit(vv[c], l0 + p));
             }
             NT::template forward<NPF>(x, tid, twf, xbuf);
-#pragma unroll
-            for (int p = 0; p < NPF; ++p) {
-                const int l = l0 + p;
-                if (q <= k) {
-                    const E *kd = bk + l * N;                              // d_l of BK_{i,j}
-                    const E *ka = keyA + ((size_t)jj * 3 + l) * N;         // -a_l or pk_jj[l]
-                    if (q == 0) mac_ept<F, EPT>(C0, x[p], kd, tid);
-                    else if (q == 1) mac_ept<F, EPT>(CI, x[p], kd, tid);
-                    else mac_ept<F, EPT>(CJ, x[p], kd, tid);
-                    mac_ept<F, EPT>(V, x[p], ka, tid);
-                } else {
-                    mac_ept<F, EPT>(C0, x[p], bk + (3 + l) * N, tid);  // f0_l
-                    mac_ept<F, EPT>(CI, x[p], bk + (6 + l) * N, tid);  // f1_l
-                }
+            if (q <= k) {
+                const E *kd = bk + l0 * N;                              // d_l0.. of BK_{i,j}
+                const E *ka = keyA + ((size_t)jj * 3 + l0) * N;         // -a_l0.. or pk_jj[l0..]
+                if (q == 0) mac_npf<F, LOGN, EPT, NPF>(C0, x, kd, tid);
+                else if (q == 1) mac_npf<F, LOGN, EPT, NPF>(CI, x, kd, tid);
+                else mac_npf<F, LOGN, EPT, NPF>(CJ, x, kd, tid);
+                mac_npf<F, LOGN, EPT, NPF>(V, x, ka, tid);
+            } else {
+                mac_npf<F, LOGN, EPT, NPF>(C0, x, bk + (3 + l0) * N, tid);  // f0_l0..
+                mac_npf<F, LOGN, EPT, NPF>(CI, x, bk + (6 + l0) * N, tid);  // f1_l0..
             }
         }
         // Inverse transforms due after this slot (two call sites):

@@ -46,7 +46,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(uint32_t k, uint32_t n) 
     ClusterLayout L;
     L.acc = 0;
     L.xbuf = L.acc + sizeof(uint32_t) * N;
-    L.vbuf = L.xbuf + sizeof(E) * 3 * N;        // three polynomials per forward pass
+    L.vbuf = L.xbuf + sizeof(E) * 3 * (N + N / 16);  // three padded polynomials per forward pass
     L.wbuf = L.vbuf + sizeof(E) * (k + 1) * N;  // CTA 0: the k+1 shares of v
     L.abar = L.wbuf + sizeof(E) * 3 * N;        // CTA 0 and CTA i: NTT(w_l)
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
@@ -129,11 +129,8 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
                     for (int p = 0; p < 3; ++p) x[p][c] = F::from_digit(G.digit(D, p));
                 }
                 NT::template forward<3>(x, tid, twf, xbuf);
-#pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    mac8<F>(C, x[l], bk + l * N, tid);                             // d_l
-                    mac8<F>(V, x[l], keyA + ((size_t)jj * 3 + l) * N, tid);        // -a_l or pk_jj[l]
-                }
+                mac_npf<F, LOGN, 8, 3>(C, x, bk, tid);                             // d_1..d_3
+                mac_npf<F, LOGN, 8, 3>(V, x, keyA + (size_t)jj * 3 * N, tid);      // -a or pk_jj
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) vbuf0[(size_t)jj * N + 8 * tid + c] = V[c];
@@ -175,13 +172,12 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
             if (jj == 0 || jj == i) {
                 // 3. c'_0 += <w, f0>, c'_i += <w, f1>
                 const E *f = bk + (jj == 0 ? 3 : 6) * (size_t)N;
+                E w[3][8];
 #pragma unroll
-                for (int l = 0; l < 3; ++l) {
-                    E w[8];
+                for (int l = 0; l < 3; ++l)
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) w[c] = wbuf[(size_t)l * N + 8 * tid + c];
-                    mac8<F>(C, w, f + l * N, tid);
-                }
+                    for (int c = 0; c < 8; ++c) w[l][c] = wbuf[(size_t)l * N + 8 * tid + c];
+                mac_npf<F, LOGN, 8, 3>(C, w, f, tid);
                 E y[1][8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) y[0][c] = C[c];

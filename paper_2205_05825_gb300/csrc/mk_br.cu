@@ -5,6 +5,8 @@
 // is in mk_internal.h.
 #include "mk_bootstrap.cuh"
 #include "mk_bootstrap_fft.cuh"
+#include "mk_bootstrap_split.cuh"
+#include "mk_bootstrap_staged.cuh"
 
 #ifndef MK_LOGN
 #error "compile with -DMK_LOGN=<log2 N> -DMK_VARIANT=<v>"
@@ -36,8 +38,29 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
 #else
     using F = br::FieldDual;
 #endif
-    return br::launch_bootstrap<F, MK_LOGN, NPF, MINB, TWG, EPT>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
-                                                                 acc_out, count, st);
+    if constexpr (kVariantKind[MK_VARIANT] == 1) {
+        (void)MINB;
+        (void)TWG;
+        (void)EPT;
+        return br::launch_staged<F, MK_LOGN, NPF>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
+                                                  st);
+    } else if constexpr (kVariantKind[MK_VARIANT] == 2 && MK_FIELD == 1) {
+        (void)TWG;
+        (void)EPT;
+        return br::launch_split<MK_LOGN, NPF, MINB>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
+                                                    st);
+    } else if constexpr (kVariantKind[MK_VARIANT] == 2) {  // no split form of the one-prime field: variant 2's kernel
+        (void)NPF;
+        (void)MINB;
+        (void)TWG;
+        (void)EPT;
+        return br::launch_bootstrap<F, MK_LOGN, kVariantNpf[2], kVariantMinBlocks[2], kVariantTwg[2] != 0,
+                                    kVariantEpt[2]>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out, count,
+                                                    st);
+    } else {
+        return br::launch_bootstrap<F, MK_LOGN, NPF, MINB, TWG, EPT>(S, K, desc, ct_a, ct_b, abar_in, max_steps,
+                                                                     ext, acc_out, count, st);
+    }
 #endif
 }
 }  // namespace mk

@@ -150,7 +150,11 @@ struct HostNtt32 {
         logN = 0;
         while ((1u << logN) < N) ++logN;
         if ((p - 1) % (2 * N) != 0) return false;
-        const uint32_t psi = powm(3, (p - 1) / (2 * N), p);  // 3 generates both primes' groups
+        // g^((p-1)/2N) for a quadratic non-residue g is a primitive 2N-th root
+        // of unity (2N is a power of two dividing p - 1).
+        uint32_t g = 2;
+        while (g < 1000 && powm(g, (p - 1) / 2, p) != p - 1) ++g;
+        const uint32_t psi = powm(g, (p - 1) / (2 * N), p);
         if (powm(psi, N, p) != p - 1) return false;
         const uint32_t psi_inv = powm(psi, p - 2, p);
         psi_rev.assign(N, 0);
@@ -180,13 +184,18 @@ struct HostNtt32 {
             }
         }
     }
-    // Device form of a key polynomial: NTT of (src mod p), times N^-1, in
-    // Montgomery form (times 2^32 mod p).
+    // Device form of a key polynomial: NTT of its coefficients taken as
+    // signed 32-bit integers (the same values mod 2^32; |c| <= 2^31 keeps the
+    // product sums within the CRT range), times N^-1, in Montgomery form
+    // (times 2^32 mod p).
     void to_device(const uint32_t *src, uint32_t *dst, bool negate) const {
         std::vector<uint32_t> a(N);
         for (uint32_t j = 0; j < N; ++j) {
-            const uint32_t r = src[j] % p;
-            a[j] = negate ? (r == 0 ? 0 : p - r) : r;
+            int64_t v = (int32_t)src[j];
+            if (negate) v = -v;
+            int64_t r = v % (int64_t)p;
+            if (r < 0) r += p;
+            a[j] = (uint32_t)r;
         }
         forward(a.data());
         const uint32_t scale = (uint32_t)(((uint64_t)n_inv << 32) % p);
@@ -304,6 +313,9 @@ struct mk_ctx {
     uint64_t *d_bk = nullptr;   // [k][n][3][d][N]
     uint64_t *d_keyA = nullptr; // [(k+1)][d][N]
     uint32_t *d_ks = nullptr;   // [k][N][t][B'-1][n+1]
+    uint32_t *d_status = nullptr;  // status word of the kernels' bounded waits (bit 0: one ran out)
+    uint64_t wait_ns = 1000000000ull;  // bound on each such wait (1 s)
+    int64_t debug_skip_key_step = -1;  // test hook of the staged kernel (see LaunchShape)
     void *d_tcws = nullptr;     // MK_FORM_TC wave workspace for tc_ws_gates gates
     uint32_t tc_ws_gates = 0;
     uint32_t *d_ext = nullptr;  // scratch [scratch_gates][k*N+1]
@@ -334,12 +346,15 @@ struct mk_ctx {
         const uint32_t cmax = cluster_mode == MK_CLUSTER_ON ? 0xFFFFFFFFu
                               : cluster_mode == MK_CLUSTER_OFF ? 0u
                                                                : (P.k <= 2 ? 1u : 2u) * sm_count / (P.k + 1);
-        return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form, cmax};
+        return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form, cmax, wait_ns,
+                           debug_skip_key_step};
     }
     DeviceKeys dkeys() const {
         // twiddles: [2][N] of 8-byte (NTT) or 16-byte (NTT2) entries; FFT: one [3][N/2] table
         const size_t half = (form == MK_FORM_NTT2 ? 16 : (form == MK_FORM_FFT ? 0 : 8)) * (size_t)P.N;
-        return DeviceKeys{d_tw, (const unsigned char *)d_tw + half, d_bk, d_keyA, d_ks, d_tcws, tc_ws_gates};
+        const void *split = form == MK_FORM_NTT2 ? (const unsigned char *)d_tw + 32 * (size_t)P.N : nullptr;
+        return DeviceKeys{d_tw, (const unsigned char *)d_tw + half, d_bk, d_keyA, d_ks, d_tcws, tc_ws_gates, d_status,
+                          split};
     }
 };
 

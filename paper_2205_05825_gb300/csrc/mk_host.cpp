@@ -160,6 +160,8 @@ void free_device(mk_ctx *c) {
     cudaFree(c->d_bk);
     cudaFree(c->d_keyA);
     cudaFree(c->d_ks);
+    cudaFree(c->d_status);
+    c->d_status = nullptr;
     cudaFree(c->d_ext);
     cudaFree(c->d_desc);
     cudaFree(c->d_tcws);
@@ -204,7 +206,9 @@ int ensure_device_keys(mk_ctx *c) {
     // 8 bytes per NTT-domain coefficient (NTT forms) or per folded coefficient
     // pair half (FFT form: N/2 double2 = 8 N bytes): the same sizes.
     std::vector<uint64_t> h_bk(bk_entries * N), h_keyA(keyA_entries * N);
-    std::vector<unsigned char> h_tw(2 * (size_t)N * 16);  // the largest twiddle table of the forms
+    // The largest twiddle tables of the forms: NTT2's [2][N] uint4 plus the
+    // per-prime tables [2 directions][2 primes][N] uint2 of the split kernel.
+    std::vector<unsigned char> h_tw(4 * (size_t)N * 16);
     // src polynomial of BK entry e and of keyA entry r (negated for the CRS)
     auto bk_src = [&](size_t e) {
         const uint32_t i = (uint32_t)(e / ((size_t)n * 3 * d));
@@ -248,6 +252,12 @@ int ensure_device_keys(mk_ctx *c) {
     } else {
         if (!c->ntt_p1.N && !(c->ntt_p1.init(kP1, N) && c->ntt_p2.init(kP2, N)))
             return fail(c, MK_EPARAMS, "ring dimension not supported by the two-prime NTT");
+        // Exactness: every product sum, at most (k+1) d N 2^(bg_bit-1) 2^31 in
+        // magnitude, must lie inside the CRT range (-p1 p2 / 2, p1 p2 / 2).
+        const long double bound = (long double)(k + 1) * d * N * std::ldexp(1.0L, (int)c->P.bg_bit - 1) *
+                                  std::ldexp(1.0L, 31);
+        if (2.0L * bound >= (long double)kP1 * (long double)kP2)
+            return fail(c, MK_EPARAMS, "product sums exceed the two-prime NTT's exact range");
         uint32_t *tw = reinterpret_cast<uint32_t *>(h_tw.data());  // [2][N] of {w1, w2, w1', w2'}
         auto comp = [](uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); };  // Shoup
         for (uint32_t m = 0; m < N; ++m) {
@@ -256,6 +266,11 @@ int ensure_device_keys(mk_ctx *c) {
             const uint32_t i1 = c->ntt_p1.psi_inv_rev[m], i2 = c->ntt_p2.psi_inv_rev[m];
             ef[0] = f1, ef[1] = f2, ef[2] = comp(f1, kP1), ef[3] = comp(f2, kP2);
             ei[0] = i1, ei[1] = i2, ei[2] = comp(i1, kP1), ei[3] = comp(i2, kP2);
+            uint32_t *sp = tw + 8 * (size_t)N;  // split tables: {w, w'} at ((dir * 2 + prime) * N + m)
+            sp[2 * (0 * (size_t)N + m)] = f1, sp[2 * (0 * (size_t)N + m) + 1] = comp(f1, kP1);
+            sp[2 * (1 * (size_t)N + m)] = f2, sp[2 * (1 * (size_t)N + m) + 1] = comp(f2, kP2);
+            sp[2 * (2 * (size_t)N + m)] = i1, sp[2 * (2 * (size_t)N + m) + 1] = comp(i1, kP1);
+            sp[2 * (3 * (size_t)N + m)] = i2, sp[2 * (3 * (size_t)N + m) + 1] = comp(i2, kP2);
         }
         auto dual = [&](const uint32_t *src, uint64_t *dst, bool negate) {
             std::vector<uint32_t> r1(N), r2(N);
@@ -270,10 +285,47 @@ int ensure_device_keys(mk_ctx *c) {
         parallel_for(bk_entries, [&](size_t e) { dual(bk_src(e), h_bk.data() + e * N, false); });
         for (size_t r = 0; r < keyA_entries; ++r) dual(keyA_src(r), h_keyA.data() + r * N, r < d);
     }
+    if (c->form == MK_FORM_NTT || c->form == MK_FORM_NTT2) {
+        // The kernels' key layouts (key_unit_pos, plane_unit_pos).
+        //  NTT: 16-byte unit u (elements 2u, 2u + 1) goes to (u % 4) * (N / 8) + u / 4.
+        //  NTT2: the {r1, r2} pairs split into a plane of r1 and a plane of r2;
+        //  in each, the 16-byte unit u (elements 4u .. 4u + 3) goes to
+        //  (u % 2) * (N / 8) + u / 2.
+        const bool planes = c->form == MK_FORM_NTT2;
+        auto interleave = [N, planes](uint64_t *poly, std::vector<uint64_t> &tmp) {
+            tmp.assign(poly, poly + N);
+            const uint32_t stride = N / 8;
+            if (planes) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(tmp.data());  // {r1, r2} per element
+                uint32_t *dst = reinterpret_cast<uint32_t *>(poly);
+                for (uint32_t pl = 0; pl < 2; ++pl)
+                    for (uint32_t u = 0; u < N / 4; ++u) {
+                        const uint32_t pos = (u & 1) * stride + (u >> 1);
+                        for (uint32_t e = 0; e < 4; ++e) dst[pl * N + 4 * pos + e] = src[2 * (4 * u + e) + pl];
+                    }
+                return;
+            }
+            for (uint32_t u = 0; u < N / 2; ++u) {
+                const uint32_t pos = (u & 3) * stride + (u >> 2);
+                poly[2 * pos] = tmp[2 * u];
+                poly[2 * pos + 1] = tmp[2 * u + 1];
+            }
+        };
+        parallel_for(bk_entries, [&](size_t e) {
+            std::vector<uint64_t> tmp;
+            interleave(h_bk.data() + e * N, tmp);
+        });
+        std::vector<uint64_t> tmp;
+        for (size_t r = 0; r < keyA_entries; ++r) interleave(h_keyA.data() + r * N, tmp);
+    }
     if (!c->d_tw) MK_CUDA(c, cudaMalloc(&c->d_tw, h_tw.size()));
     if (!c->d_bk) MK_CUDA(c, cudaMalloc(&c->d_bk, h_bk.size() * 8));
     if (!c->d_keyA) MK_CUDA(c, cudaMalloc(&c->d_keyA, h_keyA.size() * 8));
     if (!c->d_ks) MK_CUDA(c, cudaMalloc(&c->d_ks, (size_t)k * c->ks_words() * 4));
+    if (!c->d_status) {
+        MK_CUDA(c, cudaMalloc(&c->d_status, 16));
+        MK_CUDA(c, cudaMemset(c->d_status, 0, 16));
+    }
     if (c->form == MK_FORM_TC && !c->d_tcws) {
         const uint32_t gates = kTcWaveGates;
         MK_CUDA(c, cudaMalloc(&c->d_tcws, tc_workspace_bytes(c->shape(), gates)));
@@ -789,6 +841,14 @@ int mk_sync(mk_ctx *c) {
         unsigned int timeout = 0;
         MK_CUDA(c, tc05_error(&timeout, true));
         if (timeout) return fail(c, MK_ETIMEOUT, "a bounded wait of the tensor-core product kernel gave up");
+    }
+    if (c->d_status) {  // the staged blind rotation's bounded waits for its key copies
+        uint32_t st = 0;
+        MK_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+        if (st) {
+            MK_CUDA(c, cudaMemset(c->d_status, 0, sizeof(st)));
+            return fail(c, MK_ETIMEOUT, "a bounded wait of the staged blind rotation for a key copy gave up");
+        }
     }
     return MK_OK;
 }

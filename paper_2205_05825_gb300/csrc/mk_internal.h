@@ -14,10 +14,13 @@ namespace mk {
 // Goldilocks prime 2^64 - 2^32 + 1: the NTT modulus of the exact product form
 // MK_FORM_NTT.
 constexpr uint64_t kGoldilocks = 0xFFFFFFFF00000001ull;
-// The two 30-bit primes of MK_FORM_NTT2 (both = 1 mod 4096, p1*p2 > 2^59):
-// residues mod p1 and p2, recombined by CRT.
-constexpr uint32_t kP1 = 1073692673u;  // 0x3fff4001
-constexpr uint32_t kP2 = 1073668097u;  // 0x3ffee001
+// The two 28-bit primes of MK_FORM_NTT2 (both = 1 mod 8192): residues mod p1
+// and p2, recombined by CRT.  p1 p2 = 7.20e16 exceeds twice the largest
+// product sum of any supported parameter set, (k+1) d N 2^(bg_bit-1) 2^31
+// <= 9 * 3 * 1024 * 2^9 * 2^31 = 3.04e16 (k <= 8, bg_bit <= 10, N <= 1024,
+// keys as signed 32-bit values).
+constexpr uint32_t kP1 = 268369921u;  // 0x0fff0001
+constexpr uint32_t kP2 = 268361729u;  // 0x0ffee001
 
 // Per-gate record consumed by the fused linear + blind-rotation kernel.
 struct GateDesc {
@@ -43,6 +46,12 @@ struct DeviceKeys {
     // the wave workspace holds tc_ws_gates gates (a multiple of 64).
     void *tc_ws;
     uint32_t tc_ws_gates;
+    // The context's status word (device): kernels with bounded waits set bit 0
+    // when a wait runs out; mk_sync reports it as MK_ETIMEOUT and clears it.
+    uint32_t *status;
+    // MK_FORM_NTT2: per-prime twiddles [2 directions][2 primes][N] uint2
+    // {w, w'} for the split-prime kernel (nullptr for the other forms).
+    const void *tw_split;
 };
 
 struct LaunchShape {
@@ -52,6 +61,11 @@ struct LaunchShape {
     // Batches of at most this many gates run the cluster (latency) kernel of
     // the NTT forms: one CTA per accumulator polynomial (0: never).
     uint32_t cluster_max;
+    // Bound on each wait of the staged kernel for a key copy, in ns of global
+    // time, and a test hook: the key copies of this CMux step are never
+    // issued, so the waits for them run out (-1: none).
+    uint64_t wait_ns;
+    int64_t skip_key_step;
 };
 
 // a1-a8: linear part, window shift, modulus switch, blind rotation (NTT form),
@@ -75,13 +89,19 @@ cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, c
 // where the twiddles live (0: a shared-memory copy per CTA, 1: global memory
 // through the read-only cache), and the elements each thread holds per
 // polynomial (8: N/8 threads per gate, three stages per register pass; 4:
-// N/4 threads, two stages per pass, fewer registers per thread).  All give
+// N/4 threads, two stages per pass, fewer registers per thread).  Kinds:
+// 0 gives each gate its own CTA (mk_bootstrap.cuh); 1 is the staged kernel
+// (mk_bootstrap_staged.cuh: G gates per CTA share each step's key entry,
+// bulk-copied into shared memory once); 2 is the split-prime kernel
+// (mk_bootstrap_split.cuh, MK_FORM_NTT2: one half of a gate's threads per
+// prime; MK_FORM_NTT runs variant 2's kernel for these numbers).  All give
 // identical results.
-constexpr int kNumVariants = 6;
-constexpr int kVariantNpf[kNumVariants] = {3, 1, 3, 3, 3, 3};
-constexpr int kVariantMinBlocks[kNumVariants] = {3, 4, 3, 4, 2, 3};
-constexpr int kVariantTwg[kNumVariants] = {0, 1, 1, 1, 1, 1};
-constexpr int kVariantEpt[kNumVariants] = {8, 8, 8, 8, 4, 4};
+constexpr int kNumVariants = 9;
+constexpr int kVariantNpf[kNumVariants] = {3, 1, 3, 3, 3, 3, 3, 3, 3};
+constexpr int kVariantMinBlocks[kNumVariants] = {3, 4, 3, 4, 2, 3, 1, 2, 3};
+constexpr int kVariantTwg[kNumVariants] = {0, 1, 1, 1, 1, 1, 1, 1, 1};
+constexpr int kVariantEpt[kNumVariants] = {8, 8, 8, 8, 4, 4, 8, 8, 8};
+constexpr int kVariantKind[kNumVariants] = {0, 0, 0, 0, 0, 0, 1, 2, 2};
 static_assert(kNumVariants == MK_NUM_VARIANTS, "variant count of the ABI");
 
 // Per-(ring dimension, variant) blind-rotation launchers, one translation unit
@@ -97,7 +117,8 @@ static_assert(kNumVariants == MK_NUM_VARIANTS, "variant count of the ABI");
                                                           uint32_t count, cudaStream_t st);
 #define MK_DECLARE_BOOTSTRAP_F(LOGN, F)                                                                       \
     MK_DECLARE_BOOTSTRAP(LOGN, F, 0) MK_DECLARE_BOOTSTRAP(LOGN, F, 1) MK_DECLARE_BOOTSTRAP(LOGN, F, 2)          \
-    MK_DECLARE_BOOTSTRAP(LOGN, F, 3) MK_DECLARE_BOOTSTRAP(LOGN, F, 4) MK_DECLARE_BOOTSTRAP(LOGN, F, 5)
+    MK_DECLARE_BOOTSTRAP(LOGN, F, 3) MK_DECLARE_BOOTSTRAP(LOGN, F, 4) MK_DECLARE_BOOTSTRAP(LOGN, F, 5)          \
+    MK_DECLARE_BOOTSTRAP(LOGN, F, 6) MK_DECLARE_BOOTSTRAP(LOGN, F, 7) MK_DECLARE_BOOTSTRAP(LOGN, F, 8)
 MK_DECLARE_BOOTSTRAP_F(8, 0)
 MK_DECLARE_BOOTSTRAP_F(8, 1)
 MK_DECLARE_BOOTSTRAP_F(10, 0)

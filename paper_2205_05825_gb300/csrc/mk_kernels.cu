@@ -362,7 +362,9 @@ BootstrapFn pick(const LaunchShape &S) {
 #define MK_ROW(LOGN, F)                                                                                   \
     {launch_bootstrap_logn##LOGN##_f##F##_v0, launch_bootstrap_logn##LOGN##_f##F##_v1,                   \
      launch_bootstrap_logn##LOGN##_f##F##_v2, launch_bootstrap_logn##LOGN##_f##F##_v3,                   \
-     launch_bootstrap_logn##LOGN##_f##F##_v4, launch_bootstrap_logn##LOGN##_f##F##_v5}
+     launch_bootstrap_logn##LOGN##_f##F##_v4, launch_bootstrap_logn##LOGN##_f##F##_v5,                   \
+     launch_bootstrap_logn##LOGN##_f##F##_v6, launch_bootstrap_logn##LOGN##_f##F##_v7,                   \
+     launch_bootstrap_logn##LOGN##_f##F##_v8}
     static const BootstrapFn t8[2][kNumVariants] = {MK_ROW(8, 0), MK_ROW(8, 1)};
     static const BootstrapFn t10[2][kNumVariants] = {MK_ROW(10, 0), MK_ROW(10, 1)};
 #undef MK_ROW

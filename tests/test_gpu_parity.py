@@ -186,7 +186,7 @@ def test_full_k2_sampled_bit_exact_and_all_decrypt(full2):
     assert np.array_equal(got[idx], ref)
 
 
-FORM_VARIANTS = [(f, v) for f in ("ntt", "ntt2") for v in range(6)] + [("tc", 0), ("tc", 1)]
+FORM_VARIANTS = [(f, v) for f in ("ntt", "ntt2") for v in range(9)] + [("tc", 0), ("tc", 1)]
 
 
 @pytest.mark.parametrize("form,variant", FORM_VARIANTS)
