@@ -125,6 +125,21 @@ int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
 enum { MK_CLUSTER_AUTO = 0, MK_CLUSTER_OFF = 1, MK_CLUSTER_ON = 2 };
 int mk_ctx_set_cluster(mk_ctx *ctx, int mode);
 
+/* Test hook for the kernels' bounded waits (no paper counterpart).  Every
+ * wait of the staged blind rotation (variant 6) for a key copy and of the
+ * tcgen05 product engine (MK_FORM_TC, variant 1) gives up after wait_ns of
+ * global time (0: the default, 1 s); a kernel whose wait gave up stops its
+ * work, lets its own copies and tensor-core operations finish, and returns
+ * without its outputs; the next mk_sync reports MK_ETIMEOUT, and the context
+ * stays usable.  kind MK_FAULT_SKIP_KEY_STEP: until the next call, the staged
+ * kernel never copies the key entry of CMux step `arg` (0-based), so the
+ * waits for it run out.  kind MK_FAULT_SKIP_DIGIT_TILE: in the next tcgen05
+ * launch, the first CTA that reaches its digit tile `arg` does not load it
+ * (one shot).  MK_FAULT_NONE clears both.  Nothing here faults the device:
+ * a skipped copy is one that is never issued. */
+enum { MK_FAULT_NONE = 0, MK_FAULT_SKIP_KEY_STEP = 1, MK_FAULT_SKIP_DIGIT_TILE = 2 };
+int mk_debug_fault(mk_ctx *ctx, int kind, int64_t arg, uint64_t wait_ns);
+
 /* The k-bit operators evaluate their netlist level by level.  With graphs on
  * (the default) the level loop of each (operator, width, pairs) plan is
  * captured once as a CUDA graph on a stream the context owns and replayed on
@@ -271,6 +286,15 @@ typedef struct mk_lin { uint32_t cst; int32_t s1, s2; } mk_lin;
 int mk_gates_lin(mk_ctx *ctx, const mk_lin *d_lin, const uint32_t *d_a, const uint32_t *d_b,
                  uint32_t *d_out, size_t count);
 
+/* The linear record of one bootstrapped gate type (MK_AND..MK_XNOR) into
+ * *out (host memory): AND Eq. 6 (-1/8, 1, 1), OR Eq. 7 (1/8, 1, 1), NAND
+ * Sec. 3.2 (5/8, -1, -1), NOR (3/8, -1, -1), XOR Eq. 10 (0, 2, -2), XNOR
+ * (1/2, 2, -2); the NOR and XNOR constants are this library's readings of
+ * Eq. 9 and Eq. 11 (the printed ones fail their truth tables).  neg_a /
+ * neg_b nonzero fold a NOT (Eq. 8: 1/4 - c) of that input into the record.
+ * Needs no context.  MK_EINVAL for another type or a NULL out. */
+int mk_gate_lin(int type, int neg_a, int neg_b, mk_lin *out);
+
 /* MKNOT (Eq. 8): d_out[g] = (0, 1/4) - d_a[g]; no bootstrapping, no key
  * switching.  d_out may alias d_a. */
 int mk_not(mk_ctx *ctx, const uint32_t *d_a, uint32_t *d_out, size_t count);
@@ -380,8 +404,14 @@ int mk_stage_keyswitch(mk_ctx *ctx, const uint32_t *d_ext, uint32_t *d_out, size
  *  - The context's keys must already be on the device: make one ordinary
  *    gate call (or mk_autotune) on this context first, otherwise MK_ESTATE.
  *  - The first call on a device looks up the scratch array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *    process; make that first call before any stream capture.  The kept
+ *    address does not survive cudaDeviceReset (or any other teardown of the
+ *    device's primary context): do not call this entry point after one.
+ *  - Under MK_FORM_TC the blind rotation works in the context's tensor-form
+ *    workspace, which the context allocated together with its device keys
+ *    (so no allocation happens in the call either); the fixed array still
+ *    holds the descriptors and the extracted samples.
  *  - Every call shares the one array and it keeps the previous call's
  *    contents; the kernels write every scratch word before reading it, so
  *    nothing needs clearing.  Calls whose device work overlaps (different

@@ -78,6 +78,8 @@ _SIGS = {
     "mk_gate": (ctypes.c_int, [VP, ctypes.c_int, VP, VP, VP, ctypes.c_size_t]),
     "mk_gates": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_gates_lin": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
+    "mk_gate_lin": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, VP]),
+    "mk_debug_fault": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64]),
     "mk_not": (ctypes.c_int, [VP, VP, VP, ctypes.c_size_t]),
     "mk_gates_noalloc": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_stage_modswitch": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
@@ -242,6 +244,13 @@ class Context:
     def set_cluster(self, mode):
         """Latency (cluster) kernel: "auto" (small launches), "on" or "off"."""
         self._check(self.L.mk_ctx_set_cluster(self.h, CLUSTER_MODES[mode]), "mk_ctx_set_cluster")
+
+    FAULTS = {"none": 0, "skip_key_step": 1, "skip_digit_tile": 2}
+
+    def debug_fault(self, kind="none", arg=0, wait_ns=0):
+        """Test hook of the bounded waits (mk_debug_fault): skip one key copy
+        of the staged kernel or one digit tile of the tcgen05 engine."""
+        self._check(self.L.mk_debug_fault(self.h, self.FAULTS[kind], int(arg), int(wait_ns)), "mk_debug_fault")
 
     def set_graphs(self, on):
         """Replay each operator's level loop as a captured CUDA graph (default on)."""
@@ -440,19 +449,26 @@ class Context:
         return out
 
 
-# Linear-part records (cst, s1, s2) of the six bootstrapped gates, for
-# mk_gates_lin: Eq. 6 (AND), Eq. 7 (OR), Sec. 3.2 (NAND), Eq. 9 (NOR, 3/8),
-# Eq. 10 (XOR), Eq. 11 (XNOR, 1/2 + 2(c1 - c2)).
-GATE_LIN = {0: (0xE0000000, 1, 1), 1: (0x20000000, 1, 1), 2: (0xA0000000, -1, -1),
-            3: (0x60000000, -1, -1), 4: (0, 2, -2), 5: (0x80000000, 2, -2)}
+class MkLin(ctypes.Structure):
+    _fields_ = [("cst", ctypes.c_uint32), ("s1", ctypes.c_int32), ("s2", ctypes.c_int32)]
+
+
+def gate_lin(gate_type, neg_a=False, neg_b=False):
+    """(cst, s1, s2) of a bootstrapped gate type, from the library (mk_gate_lin)."""
+    r = MkLin()
+    rc = load().mk_gate_lin(int(gate_type), 1 if neg_a else 0, 1 if neg_b else 0, ctypes.byref(r))
+    if rc != MK_OK:
+        raise MkError("mk_gate_lin: %s" % ERRORS.get(rc, rc))
+    return r.cst, r.s1, r.s2
 
 
 def lin_records(types):
     """numpy int32 [count, 3] of (cst, s1, s2) for gate types (int array)."""
-    rec = np.array([GATE_LIN[int(t)] for t in types], dtype=np.int64).reshape(-1, 3)
+    table = {t: gate_lin(t) for t in set(int(t) for t in types)}
     out = np.zeros((len(types), 3), np.int32)
-    out[:, 0] = rec[:, 0].astype(np.uint32).view(np.int32)
-    out[:, 1:] = rec[:, 1:]
+    for g, t in enumerate(types):
+        cst, s1, s2 = table[int(t)]
+        out[g] = (np.uint32(cst).view(np.int32), s1, s2)
     return out
 
 

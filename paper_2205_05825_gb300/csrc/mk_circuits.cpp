@@ -444,3 +444,13 @@ std::vector<uint32_t> netlist_levels(const Netlist &net) {
 }
 
 }  // namespace mk
+
+extern "C" int mk_gate_lin(int type, int neg_a, int neg_b, mk_lin *out) {
+    if (type < 0 || type > 5 || !out) return MK_EINVAL;
+    mk_gate_rec g{};
+    g.op = (uint8_t)type;
+    g.neg_a = neg_a ? 1 : 0;
+    g.neg_b = neg_b ? 1 : 0;
+    *out = mk::gate_lin(g);
+    return MK_OK;
+}

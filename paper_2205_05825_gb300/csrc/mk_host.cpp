@@ -703,6 +703,29 @@ int mk_ctx_set_cluster(mk_ctx *c, int mode) {
     return MK_OK;
 }
 
+int mk_debug_fault(mk_ctx *c, int kind, int64_t arg, uint64_t wait_ns) {
+    if (!c) return MK_EINVAL;
+    if (kind != MK_FAULT_NONE && kind != MK_FAULT_SKIP_KEY_STEP && kind != MK_FAULT_SKIP_DIGIT_TILE)
+        return fail(c, MK_EINVAL, "unknown fault kind");
+    if ((kind == MK_FAULT_SKIP_KEY_STEP || kind == MK_FAULT_SKIP_DIGIT_TILE) && arg < 0)
+        return fail(c, MK_EINVAL, "fault argument must be >= 0");
+    if (kind == MK_FAULT_SKIP_DIGIT_TILE && c->device < 0) return fail(c, MK_EDEVICE, "host-only context");
+    c->wait_ns = wait_ns ? wait_ns : 1000000000ull;
+    c->debug_skip_key_step = kind == MK_FAULT_SKIP_KEY_STEP ? arg : -1;
+    if (c->device >= 0) {
+        MK_CUDA(c, cudaSetDevice(c->device));
+        MK_CUDA(c, cudaStreamSynchronize(c->stream));
+        MK_CUDA(c, tc05_arm_skip(kind == MK_FAULT_SKIP_DIGIT_TILE ? (uint32_t)arg + 1 : 0u));
+    }
+    // captured level loops hold the old launch parameters
+    for (auto &kv : c->plans)
+        if (kv.second->graph) {
+            cudaGraphExecDestroy(kv.second->graph);
+            kv.second->graph = nullptr;
+        }
+    return MK_OK;
+}
+
 int mk_ctx_set_graphs(mk_ctx *c, int on) {
     if (!c) return MK_EINVAL;
     c->use_graphs = on != 0;

@@ -162,6 +162,7 @@ struct TcArgs {
     size_t dig_zstride;
     int nchunks;
     int dig_chunks;  // digit polynomials in the whole dig array (for the tcgen05 engine's tensor map)
+    uint64_t wait_ns;  // bound on each mbarrier wait of the tcgen05 engine (global time)
 };
 // The tcgen05 engine of those products (mk_tensor_tc05.cu): G a multiple of
 // 128; one persistent CTA per SM over (coefficient tile, gate tile, output)
@@ -169,6 +170,9 @@ struct TcArgs {
 // bounded waits (0: none).
 cudaError_t launch_products_tc05(const TcArgs &A, uint32_t N, uint32_t G, int outputs, cudaStream_t st);
 cudaError_t tc05_error(unsigned int *code, bool clear);
+// Test hook: the next launch's first producer reaching its digit tile
+// tile_plus_one - 1 skips that tile's copy (0 disarms).
+cudaError_t tc05_arm_skip(uint32_t tile_plus_one);
 constexpr uint32_t kTcWaveGates = 4096;  // gates per wave of the context's workspace
 size_t tc_workspace_bytes(const LaunchShape &S, uint32_t gates);
 uint32_t tc_wave_granularity();

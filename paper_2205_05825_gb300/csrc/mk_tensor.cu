@@ -362,6 +362,7 @@ cudaError_t blind_rotate_wave(const LaunchShape &S, const DeviceKeys &K, const T
         a.dig_zstride = 3 * (size_t)Gp * N;
         a.nchunks = 3;
         a.dig_chunks = 3 * (int)(k + 1);
+        a.wait_ns = S.wait_ns;
         e = products<LOGN>(S.variant, a, Gp, 2 * (int)(k + 1), st);
         if (e != cudaSuccess) return e;
         tc_vdigits_kernel<LOGN><<<Gp, 256, 0, st>>>(k, Gp, S.bg_bit, w.V, w.Wd);
@@ -378,6 +379,7 @@ cudaError_t blind_rotate_wave(const LaunchShape &S, const DeviceKeys &K, const T
         b.dig_zstride = 0;
         b.nchunks = 3;
         b.dig_chunks = 3;
+        b.wait_ns = S.wait_ns;
         e = products<LOGN>(S.variant, b, Gp, 2, st);
         if (e != cudaSuccess) return e;
         const int next = (step + 1 < steps) ? (int)(step + 1) : -1;
@@ -456,6 +458,7 @@ cudaError_t launch_negacyclic_tc(uint32_t N, uint32_t G, uint32_t nchunks, const
     a.dig = reinterpret_cast<const uint16_t *>(d);
     a.nchunks = (int)nchunks;
     a.dig_chunks = (int)nchunks;
+    a.wait_ns = 1000000000ull;  // 1 s
     if (engine == 1) return launch_products_tc05(a, N, G, 1, st);
     cudaError_t e = N == 256 ? set_products_smem<8>() : set_products_smem<10>();
     if (e != cudaSuccess) return e;

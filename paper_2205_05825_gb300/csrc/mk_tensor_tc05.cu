@@ -29,8 +29,12 @@
 // the MMAs of one pass run, warps 0-3 drain the other half (tcgen05.ld
 // 32x32b, one row per thread, into integer sums) and build the unit arrays
 // of the pass after, then signal it through that half's ready barrier.
-// Every wait on an mbarrier is bounded; on timeout the kernel records the
-// fact and returns after releasing TMEM.
+// Every wait on an mbarrier is bounded in global time (TcArgs::wait_ns).  A
+// wait that runs out sets the CTA's abort word; every role then leaves at its
+// next wait (the other roles do not wait out their own limits), the producer
+// waits for its copies still in flight and the MMA warp for its last commit
+// (waits on the engine's own work, bounded but not cut short by the abort
+// word), the CTA records the timeout and releases TMEM on every path.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -49,7 +53,8 @@ constexpr int T5_STAGES = 4;    // digit tiles in flight: loads run two tiles ah
 constexpr int T5_WORKERS = 128;               // warps 0-3: TMEM drain (one row each), unit arrays, planes
 constexpr int T5_THREADS = T5_WORKERS + 64;   // + warp 4 (MMA issue) + warp 5 (TMA producer)
 constexpr uint32_t T5_TMEM_COLS = 512;
-constexpr uint32_t T5_WAIT_LIMIT = 1u << 26;
+constexpr uint32_t T5_SPIN_LIMIT = 1u << 30;        // backstop on the polls of one wait
+constexpr uint64_t T5_DRAIN_NS = 1000000000ull;      // bound on waits for the CTA's own copies and MMAs
 
 // Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
 // K-major, N = 128, M = 128.
@@ -57,6 +62,9 @@ constexpr uint32_t T5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T
                               ((uint32_t)(T5_M >> 4) << 24);
 
 __device__ unsigned int g_tc05_error;  // nonzero: some wait of some CTA timed out
+// Test hook, one shot: 1 + the index (within its CTA) of one digit-tile load
+// that the first producer reaching it does not issue; 0: none.
+__device__ unsigned int g_tc05_skip;
 
 template <int LOGN>
 struct T5Smem {
@@ -72,6 +80,7 @@ struct T5Smem {
     static constexpr size_t off_acc = off_r + (size_t)4 * 2 * RLEN * 2;  // integer sums [128 gates][128 rows]
     static constexpr size_t off_bar = off_acc + (size_t)T5_NG * T5_M * 4;  // mbarriers, then the TMEM address
     static constexpr int NBARS = 2 * T5_STAGES + 5;  // full[S], empty[S], done[2], ready[2], fin
+    static constexpr size_t off_abort = off_bar + 8 * NBARS + 4;  // after the TMEM address word
     static constexpr size_t used = off_bar + 8 * NBARS + 8;
     // + 1 KB to align the base; more than half of the SM: one CTA per SM,
     // so the 512 TMEM columns it allocates are always free
@@ -107,18 +116,37 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t it = 0; it < T5_WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of parity `parity` of `bar`, at most wait_ns of global
+// time.  With an abort word: give up as soon as it is set, and set it on a
+// timeout (so the CTA's other roles give up too); without one (waits on the
+// CTA's own copies and MMAs, which complete by themselves): only the bound.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t wait_ns, volatile uint32_t *abort) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0; it < T5_SPIN_LIMIT; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (abort && *abort) return false;
+        if (globaltimer() - t0 > wait_ns) break;
     }
+    if (abort) *abort = 1;
     return false;
 }
 
@@ -258,6 +286,8 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
     const uint32_t ready0 = done0 + 16;                   // ready[h]: half h drained, the units of its next pass built
     const uint32_t fin = ready0 + 16;                     // the MMA warp's last commit
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::off_bar + 8 * L::NBARS);
+    volatile uint32_t *abort = reinterpret_cast<volatile uint32_t *>(smem + L::off_abort);
+    const uint64_t wait_ns = A.wait_ns;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nch = A.nchunks, PI = 2 * nch;  // passes per item
     const int my_items = (items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -272,6 +302,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ready0 + 8 * h), "n"(T5_WORKERS) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(fin) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *abort = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tmem_slot)),
@@ -288,31 +319,37 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
     if (warp == 5) {
         // producer: tile j = gp * KSTEPS + kc into stage j % S once the MMAs
         // of tile j - S (same stage) have committed
-        uint32_t issued = 0;
+        uint32_t issued = 0, skipped = 0xFFFFFFFFu;
         for (int gp = 0; gp < PT && ok; ++gp) {
             const T5Item I = item_of<LOGN>(A, G, (int)blockIdx.x + (gp / PI) * (int)gridDim.x);
             const int c = (gp >> 1) % nch;
             for (int kc = 0; kc < KSTEPS; ++kc) {
                 const uint32_t j = (uint32_t)(gp * KSTEPS + kc), st = j % T5_STAGES;
-                if (j >= T5_STAGES && !mbar_wait(empty0 + 8 * st, ((j / T5_STAGES) - 1) & 1)) ok = false;
+                if (j >= T5_STAGES && !mbar_wait(empty0 + 8 * st, ((j / T5_STAGES) - 1) & 1, wait_ns, abort))
+                    ok = false;
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
                     break;
                 }
                 if (lane == 0) {
-                    mbar_expect_tx(full0 + 8 * st, (uint32_t)L::stage_bytes);
-                    tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)I.g0, I.chunk0 + c,
-                                full0 + 8 * st);
+                    if (g_tc05_skip == j + 1 && atomicCAS(&g_tc05_skip, j + 1, 0u) == j + 1) {
+                        skipped = j;  // test hook: this tile's copy is never issued
+                    } else {
+                        mbar_expect_tx(full0 + 8 * st, (uint32_t)L::stage_bytes);
+                        tma_load_3d(b_base + st * (uint32_t)L::stage_bytes, &dmap, kc * T5_KC, (int)I.g0,
+                                    I.chunk0 + c, full0 + 8 * st);
+                    }
                 }
                 issued = j + 1;
                 __syncwarp();
             }
         }
         // every copy issued has landed before shared memory can be released
-        // (bounded; in the normal course the MMAs consumed them all)
+        // (in the normal course the MMAs consumed them all; a stage's newest
+        // tile is the only one of it that can still be in flight)
         if (lane == 0)
             for (uint32_t j = issued > T5_STAGES ? issued - T5_STAGES : 0; j < issued; ++j)
-                mbar_wait(full0 + 8 * (j % T5_STAGES), (j / T5_STAGES) & 1);
+                if (j != skipped) mbar_wait(full0 + 8 * (j % T5_STAGES), (j / T5_STAGES) & 1, T5_DRAIN_NS, nullptr);
         __syncwarp();
     } else if (warp == 4) {
         // MMA issuer: pass gp starts once its TMEM half is drained and its
@@ -320,14 +357,14 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
         const uint64_t adesc0 = smem_desc(a_base, 128, 128);
         for (int gp = 0; gp < PT && ok; ++gp) {
             const int h = gp & 1;
-            if (!mbar_wait(ready0 + 8 * h, (gp >> 1) & 1)) ok = false;
+            if (!mbar_wait(ready0 + 8 * h, (gp >> 1) & 1, wait_ns, abort)) ok = false;
             if (!__all_sync(0xFFFFFFFFu, ok)) {
                 ok = false;
                 break;
             }
             for (int kc = 0; kc < KSTEPS; ++kc) {
                 const uint32_t j = (uint32_t)(gp * KSTEPS + kc), st = j % T5_STAGES;
-                if (!mbar_wait(full0 + 8 * st, (j / T5_STAGES) & 1)) ok = false;
+                if (!mbar_wait(full0 + 8 * st, (j / T5_STAGES) & 1, wait_ns, abort)) ok = false;
                 if (!__all_sync(0xFFFFFFFFu, ok)) {
                     ok = false;
                     break;
@@ -354,10 +391,11 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
             if (lane == 0) mma_commit(done0 + 8 * h);  // every MMA of pass gp
             __syncwarp();
         }
-        // no MMA of this CTA is in flight past this point (bounded)
+        // no MMA of this CTA is in flight past this point (the commit arrives
+        // once every earlier MMA of this thread has completed)
         if (lane == 0) {
             mma_commit(fin);
-            mbar_wait(fin, 0);
+            mbar_wait(fin, 0, T5_DRAIN_NS, nullptr);
         }
         __syncwarp();
     } else {
@@ -381,7 +419,7 @@ __global__ void __launch_bounds__(T5_THREADS, 1)
         for (int gp = 0; gp <= PT; ++gp) {
             if (gp >= 1) {
                 const int pp = gp - 1, hp = pp & 1, lp = pp % PI;  // the drained pass, its half, its index in the item
-                ok = workers_all(mbar_wait(done0 + 8 * hp, (pp >> 1) & 1));
+                ok = workers_all(mbar_wait(done0 + 8 * hp, (pp >> 1) & 1, wait_ns, abort));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll 1
@@ -490,6 +528,10 @@ cudaError_t launch_products_tc05(const TcArgs &A, uint32_t N, uint32_t G, int ou
     if (N == 256) return launch_tc05<8>(A, G, outputs, st);
     if (N == 1024) return launch_tc05<10>(A, G, outputs, st);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t tc05_arm_skip(uint32_t tile_plus_one) {
+    return cudaMemcpyToSymbol(g_tc05_skip, &tile_plus_one, sizeof(tile_plus_one));
 }
 
 cudaError_t tc05_error(unsigned int *code, bool clear) {

@@ -140,3 +140,26 @@ def test_circuit_style_setting(lib):
     assert ctx.get_circuit_style() == "shallow"
     with pytest.raises(B.MkError):
         B.circuit_netlist("add", 8, 5)
+
+
+def test_gate_lin_records_match_oracle_linear_part():
+    """mk_gate_lin (the library's Eq. 6-11 records, with NOT folded in on
+    request) gives the oracle's linear combination of two ciphertexts, for
+    every gate type and input negation."""
+    import numpy as np
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.tiny_params(2)
+    rng = np.random.default_rng(5)
+    c1 = rng.integers(0, 1 << 32, size=o.ct_width(P), dtype=np.uint64).astype(np.uint32)
+    c2 = rng.integers(0, 1 << 32, size=o.ct_width(P), dtype=np.uint64).astype(np.uint32)
+    for t in range(6):
+        for na in (False, True):
+            for nb in (False, True):
+                cst, s1, s2 = B.gate_lin(t, na, nb)
+                a = o.mk_not(P, c1) if na else c1
+                b = o.mk_not(P, c2) if nb else c2
+                assert np.array_equal(o.lin_comb(P, cst, s1, c1, s2, c2), o.gate_linear(P, t, a, b))
+    with pytest.raises(B.MkError):
+        B.gate_lin(6)
