@@ -13,6 +13,17 @@ blind rotation (exact NTT form), SampleExtract, key switch.
 on the host cores over a bounded sample of the same workload.  Under torchrun
 every rank runs its own 4096-gate batch on its own GPU (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
+
+Besides the timed k = 2 steps the line carries, measured after them: the
+four-party half of the metric ("k4": batched gates/s over several batches,
+p50/p99, the one-gate-per-launch rate and the blind rotation's roofline) and
+bounded summaries of the other configurations -- the precision sweep
+(512 joint-key gates per party count and product form), the regression
+application (shallow netlists), the k-bit operators (8-bit throughput,
+16-bit single-pair latency, both netlist families) and the serving loop
+(k = 4, 16-bit requests, a closed batch and Poisson arrivals at 0.5 and 0.9
+of its capacity).  --sweep, --regression and --operators run the full
+versions; --no-extras leaves the summaries out.
 """
 import argparse
 import hashlib
@@ -187,7 +198,7 @@ def ncu_traffic_per_gate():
 
 
 # ----------------------------------------------------------------------------- regression application
-def run_regression(dev_index):
+def run_regression(dev_index, styles=("array", "shallow")):
     """Training and evaluation times of the encrypted linear regression at
     the full parameter set, k = 2: x encrypted by party 0, y by party 1, m = 8
     points on y = 2x + 1 (Sec. 5.5, Table 8), with each operator netlist
@@ -220,7 +231,7 @@ def run_regression(dev_index):
 
     dec = lambda ct: int(G.decrypt_integers(ctx, ct)[0])  # noqa: E731
     out = {"parties": 2, "m": len(xs)}
-    for style in ("array", "shallow"):
+    for style in styles:
         ctx.set_circuit_style(style)
         cx = G.encrypt_integers(ctx, xs, 8, 0, W.encryption_seed(70, 0), device=dev)
         cy = G.encrypt_integers(ctx, ys, 8, 1, W.encryption_seed(70, 1), device=dev)
@@ -242,6 +253,133 @@ def run_regression(dev_index):
     out["paper_table8_k2"] = {"formula_train_s": 227.467, "formula_eval_s": 37.131, "gd_train_s_per_iter": 1133.33,
                               "gd_eval_s": 190.644, "note": "Xeon Gold 5220 CPU; the paper does not state its data size"}
     return out
+
+
+# ----------------------------------------------------------------------------- operators (config 3)
+def run_operators(dev_index, full=False):
+    """k-bit operators (Alg. 3-6) at the full parameter set, k = 2 (and k = 4
+    with full=True).  Default (bounded): throughput of 8-bit add and multiply
+    over 64 pairs (array netlists), and the latency of one pair of each
+    16-bit operator with both netlist families.  full=True: the config-3
+    table, every operator at 8 and 16 bits over 256 pairs, k = 2 and 4, both
+    families.  Wall-clock seconds with the device synchronised on both sides;
+    every output decrypted against native two's-complement arithmetic."""
+    import torch
+
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    dev = "cuda:%d" % dev_index
+    if full:
+        cases = [(k, style, op, bits, 256) for k in (2, 4) for style in ("array", "shallow")
+                 for bits in (8, 16) for op in ("add", "sub", "mul", "div")]
+    else:
+        cases = ([(2, "array", op, 8, 64) for op in ("add", "mul")] +
+                 [(2, style, op, 16, 1) for style in ("array", "shallow") for op in ("add", "sub", "mul", "div")])
+    out = []
+    ctxs = {}
+    for k, style, op, bits, pairs in cases:
+        if k not in ctxs:
+            for c_ in ctxs.values():
+                c_.close()
+            ctxs = {}
+            P = W.full_params(k)
+            ctx = B.Context(P, W.CRS_SEED, device=dev_index)
+            for i, s_ in enumerate(W.party_seeds(k)):
+                ctx.keygen(i, s_)
+            ctx.autotune(1024)
+            ctxs[k] = ctx
+        ctx = ctxs[k]
+        ctx.set_circuit_style(style)
+        a, b = W.random_operands(bits, pairs, config_id=3)
+        if op == "div":
+            b = np.where(b == 0, 1, b)
+        ca = ctx.encrypt(0, W.int_to_bits(a, bits).ravel(), W.encryption_seed(80, 0)).reshape(pairs, bits, -1)
+        cb = ctx.encrypt(1, W.int_to_bits(b, bits).ravel(), W.encryption_seed(80, 1)).reshape(pairs, bits, -1)
+        da = torch.from_numpy(ca.view(np.int32)).to(dev)
+        db = torch.from_numpy(cb.view(np.int32)).to(dev)
+        nout = 2 * bits if op == "mul" else bits
+        o1 = torch.zeros((pairs, nout, ctx.W), dtype=torch.int32, device=dev)
+        o2 = torch.zeros((pairs, bits, ctx.W), dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if op == "div":
+            ctx.div_kbit(bits, da, db, o1, o2)
+        else:
+            getattr(ctx, op + "_kbit")(bits, da, db, o1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        got = W.bits_to_int(ctx.decrypt(o1).reshape(pairs, -1))
+        if op == "div":
+            r = W.bits_to_int(ctx.decrypt(o2).reshape(pairs, -1))
+            exp = [W.expected_result(op, int(x), int(y), bits) for x, y in zip(a, b)]
+            ok = all((int(q), int(rr)) == e for q, rr, e, x, y in zip(got, r, exp, a, b)
+                     if not (x == -(1 << (bits - 1)) and y == -1))
+        else:
+            ok = all(int(g) == W.expected_result(op, int(x), int(y), bits) for g, x, y in zip(got, a, b))
+        net = B.circuit_netlist(op, bits, style)
+        gates = len(net["gates"]) * pairs
+        out.append({"parties": k, "style": style, "op": op, "bits": bits, "pairs": pairs, "netlist_gates":
+                    len(net["gates"]), "levels": net["levels"], "seconds": dt, "gates_per_s": gates / dt,
+                    "s_per_level": dt / max(net["levels"], 1), "decrypt_ok": bool(ok)})
+        ctx.set_circuit_style("array")
+    for c_ in ctxs.values():
+        c_.close()
+    return out
+
+
+def run_sweep(dev_index, gates, forms, parties=(2, 4, 8), autotune=True):
+    """Precision sweep (config 4): gates/s of each product form at 2, 4 and 8
+    parties, joint-key inputs (all k n CMux steps run), every output
+    decrypted."""
+    import torch
+
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    out = []
+    for kk in parties:
+        Pk = W.full_params(kk)
+        ck = B.Context(Pk, W.CRS_SEED, device=dev_index)
+        for i, s_ in enumerate(W.party_seeds(kk)):
+            ck.keygen(i, s_)
+        ts, x1, x2 = W.random_gates(gates, config_id=40 + kk)
+        e1 = ck.encrypt_joint(x1, W.encryption_seed(40 + kk, 0))
+        e2 = ck.encrypt_joint(x2, W.encryption_seed(40 + kk, 1))
+        tr = np.array([[a & b, a | b, 1 - (a & b), 1 - (a | b), a ^ b, 1 - (a ^ b)][t]
+                       for t, a, b in zip(ts, x1.astype(int), x2.astype(int))], np.uint8)
+        cuda = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32  # noqa: E731
+                                          else np.ascontiguousarray(a)).cuda()
+        dt_, d1, d2 = cuda(ts.astype(np.uint8)), cuda(e1), cuda(e2)
+        do = torch.zeros((gates, ck.W), dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        for form in forms:
+            Gf = gates if form != "tc" else min(gates, 2048)  # the O(N^2) form: at most one 2048-gate wave
+            ck.set_form(form)
+            if autotune:
+                ck.autotune(1024)
+            else:
+                ck.set_variant(1 if form == "tc" else 2)
+            ck.gates(dt_[:Gf], d1[:Gf], d2[:Gf], do[:Gf])
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            ck.gates(dt_[:Gf], d1[:Gf], d2[:Gf], do[:Gf])
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ms = s0.elapsed_time(s1)
+            out.append({"parties": kk, "form": form, "gates": Gf, "gates_per_s": Gf / (ms * 1e-3),
+                        "decrypt_ok": bool(np.array_equal(ck.decrypt(do[:Gf]), tr[:Gf])),
+                        "active_cmux_steps_per_gate": kk * Pk["n"]})
+        ck.close()
+    return out
+
+
+def guarded(fn):
+    """Run an optional part of the report; its failure is recorded, not fatal."""
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001
+        return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -371,72 +509,89 @@ def run_ours(args):
     plain_rate = plain_g / (plain_ms * 1e-3)
     ctx.set_batch(4096)
 
-    # k = 4 parties (second half of the metric): one timed batch
+    scale = 1e12 if args.form == "tc" else 1e9
+    ceiling = (B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / scale
+               * UNITS_PER_BUTTERFLY[args.form])
+
+    # k = 4 parties (second half of the metric): several timed batches, the
+    # blind rotation's roofline, and the one-gate-per-launch form
     k4 = None
     if args.k4_gates > 0:
-        P4, ctx4, t4, a4, b4, tr4 = setup(4, args.k4_gates)
+        G4 = args.k4_gates
+        P4, ctx4, t4, a4, b4, tr4 = setup(4, G4)
         ctx4.set_form(args.form)
-        ctx4.autotune(min(args.autotune_gates, args.k4_gates))
+        v4, _ = ctx4.autotune(min(args.autotune_gates, G4))
         dt4, da4, db4 = tdev(t4.astype(np.uint8)), tdev(a4), tdev(b4)
-        do4 = torch.zeros((args.k4_gates, ctx4.W), dtype=torch.int32, device="cuda")
+        do4 = torch.zeros((G4, ctx4.W), dtype=torch.int32, device="cuda")
         ctx4.gates(dt4, da4, db4, do4)
         torch.cuda.synchronize()
-        q0 = torch.cuda.Event(enable_timing=True)
-        q1 = torch.cuda.Event(enable_timing=True)
-        q0.record(stream)
-        ctx4.gates(dt4, da4, db4, do4)
-        q1.record(stream)
+        k4_steps = max(3, min(args.steps, 5))
+        ev4 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k4_steps)]
+        ctx4.timing_enable(True)
+        ctx4.timing_reset()
+        for e_a, e_b in ev4:
+            e_a.record(stream)
+            ctx4.gates(dt4, da4, db4, do4)
+            e_b.record(stream)
         torch.cuda.synchronize()
-        k4_ms = q0.elapsed_time(q1)
+        ms4 = sorted(a_.elapsed_time(b_) for a_, b_ in ev4)
+        br4_ms, br4_n = ctx4.timing_read(0)
+        ctx4.timing_enable(False)
         k4_ok = bool(np.array_equal(ctx4.decrypt(do4), tr4))
-        k4 = {"gates_per_s": args.k4_gates / (k4_ms * 1e-3), "gates": args.k4_gates, "ms_per_batch": k4_ms,
-              "decrypt_ok": k4_ok, "active_cmux_steps_per_gate": 4 * P4["n"], "inputs": "joint-key"}
+        rate4 = G4 * len(ms4) / (sum(ms4) * 1e-3)
+        ctx4.set_batch(1)
+        ctx4.gates(dt4[:1], da4[:1], db4[:1], do4[:1])
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        ctx4.gates(dt4[:plain_g].contiguous(), da4[:plain_g].contiguous(), db4[:plain_g].contiguous(),
+                   do4[:plain_g])
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain4_ms = p0.elapsed_time(p1)
+        plain4 = plain_g / (plain4_ms * 1e-3)
+        ctx4.set_batch(4096)
+        work4 = work_per_cmux(P4, args.form) * P4["k"] * P4["n"]
+        ach4 = G4 * work4 / (br4_ms / max(br4_n, 1) * 1e-3) / scale
+        k4 = {"gates_per_s": rate4, "gates": G4, "steps": len(ms4), "ms_per_batch": float(np.mean(ms4)),
+              "latency_ms": {"p50": float(np.percentile(ms4, 50)), "p99": float(np.percentile(ms4, 99))},
+              "decrypt_ok": k4_ok, "active_cmux_steps_per_gate": 4 * P4["n"], "inputs": "joint-key",
+              "sigma_rlwe": P4["sigma_rlwe"], "variant": v4,
+              "plain_one_gate_per_launch": {"gates_per_s": plain4, "gates": plain_g,
+                                            "latency_ms": plain4_ms / plain_g, "batched_over_plain": rate4 / plain4},
+              "roofline": {"bound": "tensor" if args.form == "tc" else "alu", "achieved": ach4, "peak": ceiling,
+                           "unit": UNIT_NAME[args.form], "frac": ach4 / ceiling,
+                           "algorithmic_work_per_gate": work4, "br_share_of_step": br4_ms / sum(ms4)}}
         ctx4.close()
 
-    # precision sweep: gates/s of every product form at 2, 4 and 8 parties
+    # Bounded summaries of the other configurations, outside the timed region
+    # (--no-extras leaves them out; --sweep / --regression / --operators run
+    # the full versions).
+    extras = not args.no_extras
     sweep = None
     if args.sweep:
-        sweep = []
-        for kk in (2, 4, 8):
-            Pk = W.full_params(kk)
-            ck = B.Context(Pk, W.CRS_SEED, device=dev_index)
-            for i, s_ in enumerate(W.party_seeds(kk)):
-                ck.keygen(i, s_)
-            Gs = 8192
-            ts, x1, x2 = W.random_gates(Gs, config_id=40 + kk)
-            e1 = ck.encrypt_joint(x1, W.encryption_seed(40 + kk, 0))
-            e2 = ck.encrypt_joint(x2, W.encryption_seed(40 + kk, 1))
-            tr = np.array([[a & b, a | b, 1 - (a & b), 1 - (a | b), a ^ b, 1 - (a ^ b)][t]
-                           for t, a, b in zip(ts, x1.astype(int), x2.astype(int))], np.uint8)
-            dt_, d1, d2 = tdev(ts.astype(np.uint8)), tdev(e1), tdev(e2)
-            do = torch.zeros((Gs, ck.W), dtype=torch.int32, device="cuda")
-            for form in args.sweep_forms.split(","):
-                Gf = Gs if form != "tc" else 2048  # the O(N^2) form: one 2048-gate wave
-                ck.set_form(form)
-                ck.autotune(1024)
-                ck.gates(dt_[:Gf], d1[:Gf], d2[:Gf], do[:Gf])
-                torch.cuda.synchronize()
-                s0 = torch.cuda.Event(enable_timing=True)
-                s1 = torch.cuda.Event(enable_timing=True)
-                s0.record(stream)
-                ck.gates(dt_[:Gf], d1[:Gf], d2[:Gf], do[:Gf])
-                s1.record(stream)
-                torch.cuda.synchronize()
-                ms = s0.elapsed_time(s1)
-                sweep.append({"parties": kk, "form": form, "gates": Gf, "gates_per_s": Gf / (ms * 1e-3),
-                              "decrypt_ok": bool(np.array_equal(ck.decrypt(do[:Gf]), tr[:Gf])),
-                              "active_cmux_steps_per_gate": kk * Pk["n"]})
-            ck.close()
-
-    regression = run_regression(dev_index) if args.regression else None
+        sweep = guarded(lambda: run_sweep(dev_index, 8192, args.sweep_forms.split(",")))
+    elif extras:
+        sweep = guarded(lambda: run_sweep(dev_index, 512, ("ntt2", "tc", "fft"), autotune=False))
+    regression = None
+    if args.regression:
+        regression = guarded(lambda: run_regression(dev_index))
+    elif extras:
+        regression = guarded(lambda: run_regression(dev_index, styles=("shallow",)))
+    operators = None
+    if args.operators or extras:
+        operators = guarded(lambda: run_operators(dev_index, full=args.operators))
+    serving = None
+    if extras:
+        from paper_2205_05825_gb300.serving import run_serving
+        serving = guarded(lambda: run_serving(parties=4, bits=16, capacity_requests=48, requests=24,
+                                              loads=(0.5, 0.9), device=dev_index))
 
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
     mm_per_gate = work_per_cmux(P, args.form) * P["k"] * P["n"]
-    scale = 1e12 if args.form == "tc" else 1e9
     achieved = G * mm_per_gate / (avg_br_ms * 1e-3) / scale
-    ceiling = (B.measure_butterfly_rate(dev_index, stream.cuda_stream, iters=2048, form=args.form) / scale
-               * UNITS_PER_BUTTERFLY[args.form])
     traffic_pg = ncu_traffic_per_gate() if args.form == "ntt2" else None
     if args.form == "tc":
         mp = measured_peaks()
@@ -490,6 +645,8 @@ def run_ours(args):
         "k4": k4,
         "precision_sweep": sweep,
         "regression": regression,
+        "operators": operators,
+        "serving": serving,
         "decrypt_ok": bool(ok),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(G + 2 * G * ctx.W * 4),
@@ -586,6 +743,11 @@ def main():
                     help="comma-separated product forms the sweep times")
     ap.add_argument("--regression", action="store_true",
                     help="also time the encrypted linear regression (Algorithms 7 and 8) at k = 2, full size")
+    ap.add_argument("--operators", action="store_true",
+                    help="also time the config-3 operator table (every operator, 8 and 16 bits, 256 pairs, "
+                         "k = 2 and 4, both netlist families)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the bounded sweep, regression, operator and serving summaries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -78,8 +78,57 @@ def run_stream(server, client, reqs, arrivals=None):
     return done_t - submit_t, time.perf_counter() - t0
 
 
+def run_serving(parties=4, bits=16, capacity_requests=96, requests=96, loads=(0.5, 0.9), wave_gates=4096,
+                toy=False, cluster="auto", circuit_style="array", device=0, autotune_gates=1024):
+    """Capacity (everything submitted at once) and Poisson runs at the given
+    fractions of that capacity; returns a dict of throughput, p50/p99 latency
+    (overall and per operator) and decryption checks."""
+    P = W.toy_params(parties) if toy else W.full_params(parties)
+    ctx = B.Context(P, W.CRS_SEED, device=device)
+    for i, s in enumerate(W.party_seeds(parties)):
+        ctx.keygen(i, s)
+    if autotune_gates:
+        ctx.autotune(autotune_gates)
+    ctx.set_cluster(cluster)
+    ctx.set_circuit_style(circuit_style)
+    server = B.Server(ctx, wave_gates=wave_gates, pool_rows=1 << 20)
+    client = Client(ctx, bits)
+    stream = W.gd_request_stream(max(capacity_requests, requests), bits=bits)
+    mix = {op: sum(1 for r in stream if r[0] == op) for op in ("add", "sub", "mul", "div")}
+
+    def build(n, offset=0):
+        return [client.prepare(offset + i, *stream[i]) for i in range(n)]
+
+    # sustained capacity: everything submitted at t = 0 (closed batch)
+    reqs = build(capacity_requests)
+    lat, wall = run_stream(server, client, reqs)
+    capacity = len(reqs) / wall
+    ok = all(client.result(r) == W.expected_result(r["op"], r["a"], r["b"], bits) for r in reqs)
+    out = {"parties": parties, "bits": bits, "n": P["n"], "N": P["N"], "mix": mix, "cluster": cluster,
+           "circuit_style": circuit_style, "capacity_requests": capacity_requests,
+           "capacity_requests_per_s": capacity, "capacity_wall_s": wall, "decrypt_ok": ok, "loads": []}
+    for load in loads:
+        reqs = build(requests, offset=10000)
+        arr = W.poisson_arrivals(len(reqs), load * capacity)
+        lat, wall = run_stream(server, client, reqs, arr)
+        ok = all(client.result(r) == W.expected_result(r["op"], r["a"], r["b"], bits) for r in reqs)
+        per_op = {}
+        for op in ("add", "sub", "mul", "div"):
+            l_op = [lat[i] for i in range(len(reqs)) if reqs[i]["op"] == op]
+            if l_op:
+                per_op[op] = {"p50_s": float(np.percentile(l_op, 50)), "p99_s": float(np.percentile(l_op, 99)),
+                              "n": len(l_op)}
+        out["loads"].append({"load": load, "requests": len(reqs), "rate_requests_per_s": load * capacity,
+                             "throughput_requests_per_s": len(reqs) / wall,
+                             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                             "per_op": per_op, "decrypt_ok": ok, "wall_s": wall})
+    out["server"] = server.stats()
+    server.close()
+    ctx.close()
+    return out
+
+
 def main():
-    import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("--parties", type=int, default=4)
     ap.add_argument("--bits", type=int, default=16)
@@ -94,46 +143,9 @@ def main():
                     help="operator netlist family: fewest gates (array) or fewest levels (shallow)")
     args = ap.parse_args()
     B.load(build_if_missing=True)
-    P = W.toy_params(args.parties) if args.toy else W.full_params(args.parties)
-    ctx = B.Context(P, W.CRS_SEED, device=0)
-    for i, s in enumerate(W.party_seeds(args.parties)):
-        ctx.keygen(i, s)
-    ctx.autotune(1024)
-    ctx.set_cluster(args.cluster)
-    ctx.set_circuit_style(args.circuit_style)
-    server = B.Server(ctx, wave_gates=args.wave_gates, pool_rows=1 << 20)
-    client = Client(ctx, args.bits)
-    stream = W.gd_request_stream(max(args.capacity_requests, args.requests), bits=args.bits)
-    mix = {op: sum(1 for r in stream if r[0] == op) for op in ("add", "sub", "mul", "div")}
-
-    def build(n, offset=0):
-        return [client.prepare(offset + i, *stream[i]) for i in range(n)]
-
-    # sustained capacity: everything submitted at t = 0 (closed batch)
-    reqs = build(args.capacity_requests)
-    lat, wall = run_stream(server, client, reqs)
-    capacity = len(reqs) / wall
-    ok = all(client.result(r) == W.expected_result(r["op"], r["a"], r["b"], args.bits) for r in reqs)
-    out = {"parties": args.parties, "bits": args.bits, "n": P["n"], "N": P["N"], "mix": mix, "cluster": args.cluster,
-           "capacity_requests_per_s": capacity, "capacity_wall_s": wall, "decrypt_ok": ok, "loads": []}
-    for load in [float(x) for x in args.loads.split(",") if x]:
-        reqs = build(args.requests, offset=10000)
-        arr = W.poisson_arrivals(len(reqs), load * capacity)
-        lat, wall = run_stream(server, client, reqs, arr)
-        ok = all(client.result(r) == W.expected_result(r["op"], r["a"], r["b"], args.bits) for r in reqs)
-        per_op = {}
-        for op in ("add", "sub", "mul", "div"):
-            l_op = [lat[i] for i in range(len(reqs)) if reqs[i]["op"] == op]
-            if l_op:
-                per_op[op] = {"p50_s": float(np.percentile(l_op, 50)), "p99_s": float(np.percentile(l_op, 99)),
-                              "n": len(l_op)}
-        out["loads"].append({"load": load, "rate_requests_per_s": load * capacity,
-                             "throughput_requests_per_s": len(reqs) / wall,
-                             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                             "per_op": per_op, "decrypt_ok": ok, "wall_s": wall})
-    out["server"] = server.stats()
-    server.close()
-    ctx.close()
+    out = run_serving(args.parties, args.bits, args.capacity_requests, args.requests,
+                      [float(x) for x in args.loads.split(",") if x], args.wave_gates, args.toy, args.cluster,
+                      args.circuit_style)
     print(json.dumps(out), flush=True)
 
 

@@ -32,8 +32,9 @@ def _dec(ctx, ct):
     return int(G.decrypt_integers(ctx, ct)[0])
 
 
+@pytest.mark.parametrize("style", ["array", "shallow"])
 @pytest.mark.parametrize("case", ["exact line", "noisy"])
-def test_closed_form_8bit_equals_the_oracle(ctx2, case):
+def test_closed_form_8bit_equals_the_oracle(ctx2, case, style):
     from oracle import regression as R
     from paper_2205_05825_gb300 import regression as G
     from paper_2205_05825_gb300 import workloads as W
@@ -43,27 +44,36 @@ def test_closed_form_8bit_equals_the_oracle(ctx2, case):
         xs, ys = W.unary_regression_data(6, 2, 1, -3, 4, 1, config_id=61)
     k = 8
     cx, cy = _enc(ctx2, xs, ys, k, 60)
-    omega, b, calls = G.closed_form(ctx2, k, cx, cy)
-    ref = R.closed_form(xs, ys, k)
-    assert (_dec(ctx2, omega), _dec(ctx2, b)) == ref
-    if case == "exact line":
-        assert ref == (2, 1)
-    loss, _ = G.loss_closed_form(ctx2, k, cx, cy, omega, b)
-    ctx2.sync()
+    ctx2.set_circuit_style(style)
+    try:
+        omega, b, calls = G.closed_form(ctx2, k, cx, cy)
+        ref = R.closed_form(xs, ys, k)
+        assert (_dec(ctx2, omega), _dec(ctx2, b)) == ref
+        if case == "exact line":
+            assert ref == (2, 1)
+        loss, _ = G.loss_closed_form(ctx2, k, cx, cy, omega, b)
+        ctx2.sync()
+    finally:
+        ctx2.set_circuit_style("array")
     assert _dec(ctx2, loss) == R.loss_closed_form(xs, ys, ref[0], ref[1], k)
 
 
-def test_gradient_descent_16bit_equals_the_oracle(ctx2):
+@pytest.mark.parametrize("style", ["array", "shallow"])
+def test_gradient_descent_16bit_equals_the_oracle(ctx2, style):
     from oracle import regression as R
     from paper_2205_05825_gb300 import regression as G
     from paper_2205_05825_gb300 import workloads as W
     xs, ys = W.unary_regression_data(4, 2, 1, 1, 4, 0, config_id=62)
     k, n, a_num, a_den, iters = 16, 100, 1, 16, 2
     cx, cy = _enc(ctx2, xs, ys, k, 63)
-    Wc, Bc, calls = G.gradient_descent(ctx2, k, cx, cy, n, a_num, a_den, iters)
-    W_, B_ = R.gradient_descent(xs, ys, k, n, a_num, a_den, iters)
-    assert (_dec(ctx2, Wc), _dec(ctx2, Bc)) == (W_, B_)
-    assert calls["div"] == iters
-    loss, _ = G.loss_gradient_descent(ctx2, k, cx, cy, Wc, Bc, n)
-    ctx2.sync()
+    ctx2.set_circuit_style(style)
+    try:
+        Wc, Bc, calls = G.gradient_descent(ctx2, k, cx, cy, n, a_num, a_den, iters)
+        W_, B_ = R.gradient_descent(xs, ys, k, n, a_num, a_den, iters)
+        assert (_dec(ctx2, Wc), _dec(ctx2, Bc)) == (W_, B_)
+        assert calls["div"] == iters
+        loss, _ = G.loss_gradient_descent(ctx2, k, cx, cy, Wc, Bc, n)
+        ctx2.sync()
+    finally:
+        ctx2.set_circuit_style("array")
     assert _dec(ctx2, loss) == R.loss_gradient_descent(xs, ys, W_, B_, n, k)
