@@ -374,6 +374,91 @@ def run_sweep(dev_index, gates, forms, parties=(2, 4, 8), autotune=True):
     return out
 
 
+def run_table2(dev_index, batch=4096):
+    """Table 2's comparison on the GPU (full size, k = 2): each gate evaluated
+    directly (one bootstrap; NOT is linear) and as the naive scheme composes
+    it from bootstrapped NANDs alone (NOT = NAND(x, x); AND 2, OR 3, NOR 4,
+    XOR 4, XNOR 5 NANDs, in 2-4 dependent steps).  Per gate type: the
+    latency of one gate and the time per gate in a batch of `batch` gates
+    (each NAND step one batched launch), CUDA events on the stream; every
+    output decrypted against the truth table."""
+    import torch
+
+    from paper_2205_05825_gb300 import binding as B
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.full_params(2)
+    ctx = B.Context(P, W.CRS_SEED, device=dev_index)
+    for i, s_ in enumerate(W.party_seeds(2)):
+        ctx.keygen(i, s_)
+    ctx.autotune(1024)
+    dev = "cuda:%d" % dev_index
+    _, b1, b2 = W.random_gates(batch, config_id=77)
+    A = torch.from_numpy(ctx.encrypt(0, b1, W.encryption_seed(77, 0)).view(np.int32)).to(dev)
+    Bc = torch.from_numpy(ctx.encrypt(1, b2, W.encryption_seed(77, 1)).view(np.int32)).to(dev)
+    names = ["AND", "OR", "NAND", "NOR", "XOR", "XNOR", "NOT"]
+    truth = {"AND": b1 & b2, "OR": b1 | b2, "NAND": 1 - (b1 & b2), "NOR": 1 - (b1 | b2), "XOR": b1 ^ b2,
+             "XNOR": 1 - (b1 ^ b2), "NOT": 1 - b1}
+    # NAND steps of the naive scheme: (destination, first input, second input)
+    recipe = {"AND": [("n", "a", "b"), ("r", "n", "n")],
+              "OR": [("x", "a", "a"), ("y", "b", "b"), ("r", "x", "y")],
+              "NAND": [("r", "a", "b")],
+              "NOR": [("x", "a", "a"), ("y", "b", "b"), ("o", "x", "y"), ("r", "o", "o")],
+              "XOR": [("n", "a", "b"), ("x", "a", "n"), ("y", "b", "n"), ("r", "x", "y")],
+              "XNOR": [("n", "a", "b"), ("x", "a", "n"), ("y", "b", "n"), ("o", "x", "y"), ("r", "o", "o")],
+              "NOT": [("r", "a", "a")]}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()  # warm-up (plans, scratch)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) * 1e-3
+
+    rows = []
+    for name in names:
+        t = names.index(name)
+        res = {"gate": name, "nand_gates": len(recipe[name])}
+        for g in (1, batch):
+            a, b = A[:g].contiguous(), Bc[:g].contiguous()
+
+            def direct():
+                o = torch.zeros_like(a)
+                if name == "NOT":
+                    ctx.mk_not(a, o)
+                else:
+                    ctx.gate(t, a, b, o)
+                return o
+
+            def naive():
+                w = {"a": a, "b": b}
+                for dst, x, y in recipe[name]:
+                    w[dst] = torch.zeros_like(a)
+                    ctx.gate(2, w[x], w[y], w[dst])
+                return w["r"]
+
+            od, td = timed(direct)
+            on, tn = timed(naive)
+            ok = (np.array_equal(ctx.decrypt(od), truth[name][:g]) and
+                  np.array_equal(ctx.decrypt(on), truth[name][:g]))
+            key = "latency_s" if g == 1 else "s_per_gate_in_batch"
+            res[key] = {"ours": td / g, "naive": tn / g}
+            res.setdefault("decrypt_ok", True)
+            res["decrypt_ok"] = res["decrypt_ok"] and bool(ok)
+        rows.append(res)
+    ctx.close()
+    paper = {"AND": (0.238671, 0.238008), "OR": (0.584701, 0.23558), "NOT": (0.236541, 2e-06),
+             "NAND": (0.235327, 0.239638), "NOR": (0.470561, 0.236153), "XOR": (0.71246, 0.2354),
+             "XNOR": (0.710777, 0.23588)}
+    for r in rows:
+        r["paper_table2_s"] = {"naive": paper[r["gate"]][0], "ours": paper[r["gate"]][1],
+                               "note": "one gate at a time, MKTFHE on a Xeon Gold 5220, k = 2"}
+    return {"parties": 2, "batch": batch, "gates": rows}
+
+
 def guarded(fn):
     """Run an optional part of the report; its failure is recorded, not fatal."""
     try:
@@ -582,6 +667,7 @@ def run_ours(args):
     operators = None
     if args.operators or extras:
         operators = guarded(lambda: run_operators(dev_index, full=args.operators))
+    table2 = guarded(lambda: run_table2(dev_index)) if extras else None
     serving = None
     if extras:
         from paper_2205_05825_gb300.serving import run_serving
@@ -646,6 +732,7 @@ def run_ours(args):
         "precision_sweep": sweep,
         "regression": regression,
         "operators": operators,
+        "table2_gates": table2,
         "serving": serving,
         "decrypt_ok": bool(ok),
         "clocks": clk,

@@ -161,9 +161,16 @@ int mk_ctx_set_graphs(mk_ctx *ctx, int on);
  * 100 / 223).  Each level is one batched launch whatever its width, so an
  * evaluation with few pairs per level (latency-bound) runs faster with the
  * shallow family and one that fills every level (throughput-bound) with the
- * array family.  Applies to the operator calls and server requests made
- * after the change; MK_EINVAL for another value.  No paper counterpart. */
-enum { MK_CIRCUIT_ARRAY = 0, MK_CIRCUIT_SHALLOW = 1 };
+ * array family.  Two more families reproduce the paper's own constructions
+ * for comparison: MK_CIRCUIT_PAPER, the array family with the multiplier
+ * built from the paper's 0-, 1- and 2-adders (Sec. 3.3, Alg. 4: k rows of
+ * k-1 typed full adders over sign-weighted partial products, k^2 + 5k(k-1)
+ * gates against the paper's 7k(k-1)); MK_CIRCUIT_NAND, Table 2's naive
+ * scheme: the array family with every gate composed of bootstrapped NANDs
+ * (NOT included).  Applies to the operator calls and server requests made
+ * after the change; MK_EINVAL for another value.  No paper counterpart
+ * (ARRAY and PAPER are the paper's constructions). */
+enum { MK_CIRCUIT_ARRAY = 0, MK_CIRCUIT_SHALLOW = 1, MK_CIRCUIT_PAPER = 2, MK_CIRCUIT_NAND = 3 };
 int mk_ctx_set_circuit_style(mk_ctx *ctx, int style);
 int mk_ctx_get_circuit_style(const mk_ctx *ctx, int *style);
 

@@ -17,7 +17,7 @@ under these readings:
     a final remainder correction, and compensation back to two's complement;
     quotient sign = sign(a) XOR sign(b), remainder takes a's sign.
 
-Two construction families ("styles") compute the same functions:
+Four construction families ("styles") compute the same functions:
   - "array": the constructions above, with their ripple carry chains (O(k)
     levels per addition; the fewest gates);
   - "shallow": every carry chain replaced by a Sklansky parallel-prefix
@@ -31,7 +31,32 @@ Two construction families ("styles") compute the same functions:
     are folded away (AND with 0 is 0, XOR with 1 is a negated wire, ...) and
     gates whose outputs are never read are pruned.  O(log k) levels per
     addition, for 10-25 % more gates in the multiplier and divider and up to
-    60 % more in the adders.
+    60 % more in the adders;
+  - "paper": the array family's adder, subtractor and divider, and the
+    multiplier of Sec. 3.3 / Alg. 4 built from the paper's 0-, 1- and
+    2-adders (reading of the missing Fig. 1): every signal carries the sign
+    of its weight (a partial product a_j b_i weighs -2^(i+j) when exactly
+    one of i, j is k - 1); a full adder with t inputs of negative weight
+    first negates those inputs (NOT is free) and then: t = 0 both outputs
+    positive; t = 1 (the 1-adder) the sum is negated and weighs negative,
+    the carry positive; t = 2 (the 2-adder) the sum positive, the carry
+    negated and negative; t = 3 neither is negated, both negative.  The
+    k^2 partial products come first (row i, then column j); rows i = 1 ..
+    k - 1 each have k - 1 adders (column j adds the partial product of row
+    i, column j, to the running sum and carry at weight i + j; the first
+    row's carries are the constant 0), the last partial product of each row
+    passes through, and a final row of k - 1 adders ripples the sums and
+    carries of weights k .. 2k - 2 with a carry-in of 0 taken as negative,
+    so that every adder of that row is a 2-adder; its last carry, of
+    negative weight, is the sign bit of the 2k-bit product.  k rows of
+    k - 1 adders, k^2 + 5 k (k - 1) gates;
+  - "nand": the naive scheme of Table 2: the array family's netlists with
+    every gate composed of bootstrapped NAND gates only (the one gate the
+    underlying scheme provides): a negated input or output costs NAND(x, x)
+    (constants are negated for free); AND = NAND(n, n) with n = NAND(x, y);
+    OR = NAND(NAND(x, x), NAND(y, y)); NOR = NAND(o, o) with o that OR;
+    XOR = NAND(NAND(x, n), NAND(y, n)) with n = NAND(x, y); XNOR =
+    NAND(x', x') with x' that XOR.
 
 A netlist is a dict: ka, kb (input widths), gates = list of
 (op, a, neg_a, b, neg_b) with op in 0..5 (AND, OR, NAND, NOR, XOR, XNOR) and
@@ -332,13 +357,94 @@ def shallow_divider(k):
     return prune(dict(ka=k, kb=k, gates=bld.gates, outputs=qout + rout))
 
 
-STYLES = {"array": 0, "shallow": 1}
+# ----------------------------------------------------------------------------- the paper's multiplier
+def paper_multiplier(k):
+    """Array multiplier of the paper's 0-, 1- and 2-adders (module docstring)."""
+    bld = _Builder(k, k)
+    pp = [[(bld.gate(AND, bld.A[j], bld.B[i]), int((i == k - 1) != (j == k - 1))) for j in range(k)]
+          for i in range(k)]
+
+    def typed_adder(x, y, z):
+        """Signed signals (wire reference, negative weight): sum at the
+        inputs' weight and carry at the next, each with its weight's sign."""
+        t = x[1] + y[1] + z[1]
+        ins = [neg(r) if (n and t in (1, 2)) else r for r, n in (x, y, z)]
+        s, c = bld.full_adder(*ins)
+        if t == 0:
+            return (s, 0), (c, 0)
+        if t == 1:
+            return (neg(s), 1), (c, 0)
+        if t == 2:
+            return (s, 0), (neg(c), 1)
+        return (s, 1), (c, 1)
+
+    S = {w: pp[0][w] for w in range(k)}
+    C = {}
+    out = [pp[0][0]]
+    for i in range(1, k):
+        S2, C2 = {}, {}
+        for j in range(k - 1):
+            w = i + j
+            S2[w], C2[w + 1] = typed_adder(pp[i][j], S[w], C.get(w, (ZERO, 0)))
+        S2[i + k - 1] = pp[i][k - 1]
+        S, C = S2, C2
+        out.append(S[i])
+    carry = (ZERO, 1)  # a zero of negative weight: every adder of the last row is a 2-adder
+    for w in range(k, 2 * k - 1):
+        s, carry = typed_adder(S[w], C[w], carry)
+        out.append(s)
+    out.append(carry)
+    assert [n for _, n in out] == [0] * (2 * k - 1) + [1]  # two's complement: only the top bit weighs negative
+    return dict(ka=k, kb=k, gates=bld.gates, outputs=[r for r, _ in out])
+
+
+# ----------------------------------------------------------------------------- the naive NAND-only scheme
+def nand_only(net):
+    """The netlist with every gate composed of bootstrapped NANDs (module docstring)."""
+    bld = _Builder(net["ka"], net["kb"])
+    base = 2 + net["ka"] + net["kb"]
+    new_of = {}  # old wire -> new plain wire reference
+
+    def plain(w, ng):
+        r = new_of.get(w, (w, 0)) if w >= base else (w, 0)
+        if not ng:
+            return r
+        if r[0] in (0, 1):
+            return (1 - r[0], 0)  # a constant: negated for free
+        return bld.gate(NAND, r, r)
+
+    for g, (op, x, nx, y, ny) in enumerate(net["gates"]):
+        a, b = plain(x, nx), plain(y, ny)
+        if op == NAND:
+            r = bld.gate(NAND, a, b)
+        elif op == AND:
+            n = bld.gate(NAND, a, b)
+            r = bld.gate(NAND, n, n)
+        elif op in (OR, NOR):
+            r = bld.gate(NAND, bld.gate(NAND, a, a), bld.gate(NAND, b, b))
+            if op == NOR:
+                r = bld.gate(NAND, r, r)
+        else:  # XOR, XNOR
+            n = bld.gate(NAND, a, b)
+            r = bld.gate(NAND, bld.gate(NAND, a, n), bld.gate(NAND, b, n))
+            if op == XNOR:
+                r = bld.gate(NAND, r, r)
+        new_of[base + g] = r
+    outputs = [plain(w, ng) for w, ng in net["outputs"]]
+    return dict(ka=net["ka"], kb=net["kb"], gates=bld.gates, outputs=outputs)
+
+
+STYLES = {"array": 0, "shallow": 1, "paper": 2, "nand": 3}
 
 
 def build(op, k, style="array"):
-    style = {0: "array", 1: "shallow"}.get(style, style)
+    style = {v: n for n, v in STYLES.items()}.get(style, style)
     if style not in STYLES:
         raise ValueError(style)
+    if style == "nand":
+        return nand_only(build(op, k, "array"))
+    if style == "paper" and op in ("mul", 2):
+        return paper_multiplier(k)
     shallow = style == "shallow"
     if op in ("add", 0):
         return shallow_adder(k) if shallow else adder(k)

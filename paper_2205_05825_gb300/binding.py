@@ -20,7 +20,7 @@ PRESETS = {"toy": 0, "full": 1, "paper": 2}
 NUM_VARIANTS = 9
 FORMS = {"ntt": 0, "ntt2": 1, "fft": 2, "tc": 3}
 CLUSTER_MODES = {"auto": 0, "off": 1, "on": 2}
-CIRCUIT_STYLES = {"array": 0, "shallow": 1}
+CIRCUIT_STYLES = {"array": 0, "shallow": 1, "paper": 2, "nand": 3}
 
 U32P = ctypes.POINTER(ctypes.c_uint32)
 U8P = ctypes.POINTER(ctypes.c_uint8)

@@ -37,6 +37,30 @@
 // in the multiplier and divider and up to 60 % more in the adders: a level
 // is one batched launch whatever its width, so depth is what a narrow,
 // latency-bound evaluation pays for.
+// Two more families for comparison with the paper's own constructions:
+// MK_CIRCUIT_PAPER keeps the array family's adder, subtractor and divider and
+// builds the multiplier from the paper's 0-, 1- and 2-adders (Sec. 3.3,
+// Alg. 4; Fig. 1 is missing, this is a reading of its rules): each signal
+// carries the sign of its weight -- a partial product a_j b_i weighs
+// -2^(i+j) when exactly one of i, j is k - 1 -- and a full adder whose inputs
+// include t of negative weight negates them first (NOT is free) and then
+// outputs, for t = 0, 1, 2, 3: sum +, carry +; NOT(sum) -, carry + (the
+// 1-adder); sum +, NOT(carry) - (the 2-adder); sum -, carry -.  The k^2
+// partial products come first (row i, then column j); rows i = 1 .. k-1
+// have k-1 adders each (column j adds row i's partial product of column j
+// to the running sum and carry of weight i + j; the first row's carries are
+// the constant 0) and pass row i's last partial product through; a last
+// row of k-1 adders ripples the sums and carries of weights k .. 2k-2 from
+// a carry-in of 0 taken as negative, so that each of its adders is a
+// 2-adder and its final carry, of negative weight, is the sign bit of the
+// 2k-bit product: k rows of k-1 adders, k^2 + 5 k (k-1) gates.
+// MK_CIRCUIT_NAND is the naive scheme of Table 2: the array family with
+// every gate composed of bootstrapped NAND gates only, the one gate of the
+// scheme the paper starts from; a negated input or output costs NAND(x, x)
+// (a negated constant is the other constant); AND = NAND(n, n),
+// n = NAND(x, y); OR = NAND(NAND(x, x), NAND(y, y)); NOR = NAND(o, o) of that
+// OR; XOR = NAND(NAND(x, n), NAND(y, n)), n = NAND(x, y); XNOR = NAND(x', x')
+// of that XOR.
 // Levels: a gate's level is 1 + the deepest of its inputs; each level is one
 // batched bootstrap + key-switch launch over all its gates of all pairs.
 #include <algorithm>
@@ -391,10 +415,120 @@ Netlist build_divider(uint32_t k) {
     return b.net;
 }
 
+// ---------------------------------------------------------------- the paper's multiplier
+// A signal and the sign of its weight (1: it counts -2^w).
+struct Signed {
+    Wire r;
+    int negw;
+};
+
+// Full adder of three signals of one weight, typed by how many weigh
+// negative: the sum at that weight and the carry at the next, with their signs.
+std::pair<Signed, Signed> typed_adder(Builder &b, const Signed &x, const Signed &y, const Signed &z) {
+    const int t = x.negw + y.negw + z.negw;
+    const bool flip = t == 1 || t == 2;
+    const Wire ix = (flip && x.negw) ? negw(x.r) : x.r;
+    const Wire iy = (flip && y.negw) ? negw(y.r) : y.r;
+    const Wire iz = (flip && z.negw) ? negw(z.r) : z.r;
+    const std::pair<Wire, Wire> sc = b.full_adder(ix, iy, iz);
+    switch (t) {
+    case 0: return {Signed{sc.first, 0}, Signed{sc.second, 0}};
+    case 1: return {Signed{negw(sc.first), 1}, Signed{sc.second, 0}};
+    case 2: return {Signed{sc.first, 0}, Signed{negw(sc.second), 1}};
+    default: return {Signed{sc.first, 1}, Signed{sc.second, 1}};
+    }
+}
+
+bool build_paper_multiplier(uint32_t k, Netlist &out) {
+    Builder b(k, k);
+    std::vector<std::vector<Signed>> pp(k, std::vector<Signed>(k));
+    for (uint32_t i = 0; i < k; ++i)
+        for (uint32_t j = 0; j < k; ++j)
+            pp[i][j] = Signed{b.gate(OP_AND, b.A[j], b.B[i]), ((i == k - 1) != (j == k - 1)) ? 1 : 0};
+    const Signed zero{kZero, 0};
+    std::vector<Signed> S(2 * k, zero), C(2 * k, zero), res;
+    for (uint32_t w = 0; w < k; ++w) S[w] = pp[0][w];
+    res.push_back(pp[0][0]);
+    for (uint32_t i = 1; i < k; ++i) {
+        std::vector<Signed> S2(2 * k, zero), C2(2 * k, zero);
+        for (uint32_t j = 0; j + 1 < k; ++j) {
+            const uint32_t w = i + j;
+            const std::pair<Signed, Signed> sc = typed_adder(b, pp[i][j], S[w], C[w]);
+            S2[w] = sc.first;
+            C2[w + 1] = sc.second;
+        }
+        S2[i + k - 1] = pp[i][k - 1];
+        S = S2;
+        C = C2;
+        res.push_back(S[i]);
+    }
+    Signed carry{kZero, 1};  // a zero of negative weight: every adder of the last row is a 2-adder
+    for (uint32_t w = k; w + 1 < 2 * k; ++w) {
+        const std::pair<Signed, Signed> sc = typed_adder(b, S[w], C[w], carry);
+        res.push_back(sc.first);
+        carry = sc.second;
+    }
+    res.push_back(carry);
+    for (size_t w = 0; w < res.size(); ++w)  // two's complement: only the top bit weighs negative
+        if (res[w].negw != (w + 1 == res.size() ? 1 : 0)) return false;
+    for (const Signed &x : res) b.net.outputs.push_back(x.r);
+    out = b.net;
+    return true;
+}
+
+// ---------------------------------------------------------------- the naive NAND-only scheme
+Netlist nand_only(const Netlist &net) {
+    Builder b(net.ka, net.kb);
+    const int32_t base = (int32_t)(2 + net.ka + net.kb);
+    std::vector<Wire> new_of(net.gates.size());
+    auto plain = [&](int32_t w, int ng) -> Wire {
+        const Wire r = w >= base ? new_of[(size_t)(w - base)] : Wire{w, 0};
+        if (!ng) return r;
+        if (r.w <= 1) return Wire{1 - r.w, 0};  // a constant: negated for free
+        return b.gate(OP_NAND, r, r);
+    };
+    for (size_t g = 0; g < net.gates.size(); ++g) {
+        const mk_gate_rec &G = net.gates[g];
+        const Wire x = plain(G.a, G.neg_a);
+        const Wire y = plain(G.b, G.neg_b);
+        Wire r;
+        if (G.op == OP_NAND) {
+            r = b.gate(OP_NAND, x, y);
+        } else if (G.op == OP_AND) {
+            const Wire n = b.gate(OP_NAND, x, y);
+            r = b.gate(OP_NAND, n, n);
+        } else if (G.op == OP_OR || G.op == OP_NOR) {
+            const Wire nx = b.gate(OP_NAND, x, x);
+            const Wire ny = b.gate(OP_NAND, y, y);
+            r = b.gate(OP_NAND, nx, ny);
+            if (G.op == OP_NOR) r = b.gate(OP_NAND, r, r);
+        } else {  // XOR, XNOR
+            const Wire n = b.gate(OP_NAND, x, y);
+            const Wire p = b.gate(OP_NAND, x, n);
+            const Wire q = b.gate(OP_NAND, y, n);
+            r = b.gate(OP_NAND, p, q);
+            if (G.op == OP_XNOR) r = b.gate(OP_NAND, r, r);
+        }
+        new_of[g] = r;
+    }
+    for (const Wire &o : net.outputs) b.net.outputs.push_back(plain(o.w, o.neg));
+    return b.net;
+}
+
 }  // namespace
 
 bool build_netlist(int op, uint32_t k, int style, Netlist &out) {
     if (k < 2 || k > 64) return false;
+    if (style == MK_CIRCUIT_NAND) {
+        Netlist array;
+        if (!build_netlist(op, k, MK_CIRCUIT_ARRAY, array)) return false;
+        out = nand_only(array);
+        return true;
+    }
+    if (style == MK_CIRCUIT_PAPER) {
+        if (op == MK_OP_MUL) return build_paper_multiplier(k, out);
+        return build_netlist(op, k, MK_CIRCUIT_ARRAY, out);
+    }
     if (style == MK_CIRCUIT_SHALLOW) {
         switch (op) {
         case MK_OP_ADD: out = build_shallow_adder(k, false); return true;

@@ -734,7 +734,9 @@ int mk_ctx_set_graphs(mk_ctx *c, int on) {
 
 int mk_ctx_set_circuit_style(mk_ctx *c, int style) {
     if (!c) return MK_EINVAL;
-    if (style != MK_CIRCUIT_ARRAY && style != MK_CIRCUIT_SHALLOW) return fail(c, MK_EINVAL, "unknown circuit style");
+    if (style != MK_CIRCUIT_ARRAY && style != MK_CIRCUIT_SHALLOW && style != MK_CIRCUIT_PAPER &&
+        style != MK_CIRCUIT_NAND)
+        return fail(c, MK_EINVAL, "unknown circuit style");
     c->circuit_style = style;
     return MK_OK;
 }

@@ -54,7 +54,10 @@ def operands(k, count=2000):
     return W.random_operands(k, count)
 
 
-@pytest.mark.parametrize("style", ["array", "shallow"])
+STYLES = ["array", "shallow", "paper", "nand"]
+
+
+@pytest.mark.parametrize("style", STYLES)
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 8, 16])
 def test_netlist_plaintext_against_native(op, k, style):
@@ -77,18 +80,19 @@ def _value(row):
     return v - (1 << k) if row[-1] else v
 
 
-@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
-def test_shallow_netlists_at_every_width(op):
+@pytest.mark.parametrize("style,op", [("shallow", "add"), ("shallow", "sub"), ("shallow", "mul"),
+                                      ("shallow", "div"), ("paper", "mul")])
+def test_netlists_at_every_width(style, op):
     """Widths 6..64 (beyond int64 products): random and extreme operands,
     checked with Python integers."""
     rng = np.random.default_rng(7)
-    for k in range(6, 65):
+    for k in range(6, 65, 1 if style == "shallow" else 5):
         lo, hi = -(1 << (k - 1)), (1 << (k - 1)) - 1
         a = [lo, lo, hi, -1, 0] + [int(v) for v in rng.integers(-(1 << 62), 1 << 62, size=6) >> max(0, 63 - k)]
         b = [1, hi, lo, -1, 5] + [int(v) | 1 for v in rng.integers(-(1 << 62), 1 << 62, size=6) >> max(0, 63 - k)]
         A = np.array([[(x >> i) & 1 for i in range(k)] for x in a])
         B_ = np.array([[(y >> i) & 1 for i in range(k)] for y in b])
-        out = C.eval_plain(C.build(op, k, "shallow"), A, B_)
+        out = C.eval_plain(C.build(op, k, style), A, B_)
         for row, x, y in zip(out, a, b):
             if op == "add":
                 assert _value(row) == ((x + y - lo) % (1 << k)) + lo
@@ -116,7 +120,7 @@ def test_shallow_family_is_shallower():
     assert depth[("div", 8)] == (236, 100) and depth[("div", 16)] == (852, 223)
 
 
-@pytest.mark.parametrize("style", ["array", "shallow"])
+@pytest.mark.parametrize("style", STYLES)
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8, 12, 16, 17, 31, 33, 64])
 def test_library_netlist_equals_oracle_netlist(op, k, style):
@@ -150,6 +154,39 @@ def test_gate_counts_against_the_paper():
             assert ours > 0
     assert len(C.build("mul", 8)["gates"]) == 325       # paper: 392
     assert len(C.build("div", 8)["gates"]) == 649       # paper: 7*64 + 17 = 465
+
+
+def test_paper_multiplier_structure():
+    """The 0/1/2-adder multiplier: k^2 partial products and k rows of k - 1
+    full adders (5 gates each), against the paper's 7 k (k - 1) (two AND
+    gates per adder); the adder types follow the paper's rules, so the last
+    row is 2-adders only."""
+    for k in (2, 4, 8, 16):
+        net = C.build("mul", k, "paper")
+        assert len(net["gates"]) == k * k + 5 * k * (k - 1)
+        assert sum(1 for g in net["gates"] if g[0] == C.AND) == k * k + 2 * k * (k - 1)
+    assert len(C.build("mul", 8, "paper")["gates"]) == 344    # paper: 7 * 8 * 7 = 392
+
+
+def test_nand_family_uses_nand_gates_only():
+    """Table 2's naive scheme: only NAND gates, no negated input or output
+    (a NOT is a bootstrapped NAND(x, x)), and per gate type the composition
+    costs 1 (NAND), 2 (AND), 3 (OR), 4 (NOR, XOR), 5 (XNOR) NANDs."""
+    for op in ("add", "sub", "mul", "div"):
+        net = C.build(op, 8, "nand")
+        assert all(g[0] == C.NAND for g in net["gates"])
+        assert all(g[2] == 0 and g[4] == 0 for g in net["gates"] if g[1] > 1 and g[3] > 1)
+        assert all(ng == 0 for w, ng in net["outputs"] if w > 1)
+    cost = {}
+    for t, name in enumerate(("AND", "OR", "NAND", "NOR", "XOR", "XNOR")):
+        one = dict(ka=1, kb=1, gates=[(t, 2, 0, 3, 0)], outputs=[(4, 0)])
+        net = C.nand_only(one)
+        cost[name] = len(net["gates"])
+        for x in (0, 1):
+            for y in (0, 1):
+                assert (C.eval_plain(net, [[x]], [[y]])[0][0] == C.eval_plain(one, [[x]], [[y]])[0][0])
+    assert cost == {"AND": 2, "OR": 3, "NAND": 1, "NOR": 4, "XOR": 4, "XNOR": 5}
+    assert len(C.nand_only(dict(ka=1, kb=1, gates=[], outputs=[(2, 1)]))["gates"]) == 1  # NOT = NAND(x, x)
 
 
 @pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])

@@ -61,7 +61,7 @@ def toy(gpu_ready):
     return P, keys, _ctx(P, keys)
 
 
-STYLES = ["array", "shallow"]
+STYLES = ["array", "shallow", "paper", "nand"]
 
 
 @pytest.mark.parametrize("style", STYLES)
@@ -109,12 +109,15 @@ def full2(gpu_ready):
 
 # Full size (config 3): every operator at 8 and 16 bits for both netlist
 # families at two parties, and at four parties with the shallow family (few
-# pairs: a call costs its netlist depth in launches whatever its width).
+# pairs: a call costs its netlist depth in launches whatever its width); the
+# paper's 0/1/2-adder multiplier and the NAND-only family.
 FULL_CASES = ([("array", 2, op, 8, pr) for op, pr in (("add", 64), ("sub", 64), ("mul", 32), ("div", 16))] +
               [("array", 2, op, 16, pr) for op, pr in (("add", 16), ("sub", 16), ("mul", 8), ("div", 4))] +
               [("shallow", 2, op, kb, 8) for kb in (8, 16) for op in ("add", "sub", "mul", "div")] +
               [("shallow", 4, op, kb, 4) for kb in (8, 16) for op in ("add", "sub", "mul", "div")] +
-              [("array", 4, op, 8, 16) for op in ("add", "sub", "mul", "div")])
+              [("array", 4, op, 8, 16) for op in ("add", "sub", "mul", "div")] +
+              [("paper", 2, "mul", 8, 16), ("paper", 2, "mul", 16, 4), ("paper", 4, "mul", 8, 4),
+               ("nand", 2, "add", 8, 8), ("nand", 2, "mul", 8, 4)])
 
 
 @pytest.fixture(scope="module")
