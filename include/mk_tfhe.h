@@ -135,9 +135,12 @@ int mk_ctx_set_cluster(mk_ctx *ctx, int mode);
  * kernel never copies the key entry of CMux step `arg` (0-based), so the
  * waits for it run out.  kind MK_FAULT_SKIP_DIGIT_TILE: in the next tcgen05
  * launch, the first CTA that reaches its digit tile `arg` does not load it
- * (one shot).  MK_FAULT_NONE clears both.  Nothing here faults the device:
- * a skipped copy is one that is never issued. */
-enum { MK_FAULT_NONE = 0, MK_FAULT_SKIP_KEY_STEP = 1, MK_FAULT_SKIP_DIGIT_TILE = 2 };
+ * (one shot).  kind MK_FAULT_SKIP_WIRE_READY: until the next call, the
+ * persistent operator launch never marks the output of its work item `arg`
+ * (0-based, in the plan's level order) ready, so once every other gate has
+ * finished, the gates that read it give up after the bound.  MK_FAULT_NONE clears all three.  Nothing here
+ * faults the device: a skipped copy or mark is one that is never issued. */
+enum { MK_FAULT_NONE = 0, MK_FAULT_SKIP_KEY_STEP = 1, MK_FAULT_SKIP_DIGIT_TILE = 2, MK_FAULT_SKIP_WIRE_READY = 3 };
 int mk_debug_fault(mk_ctx *ctx, int kind, int64_t arg, uint64_t wait_ns);
 
 /* The k-bit operators evaluate their netlist level by level.  With graphs on
@@ -148,6 +151,22 @@ int mk_debug_fault(mk_ctx *ctx, int kind, int64_t arg, uint64_t wait_ns);
  * (mk_timing_enable) or with MK_FORM_TC.  No paper counterpart: launch
  * overhead only, results are identical either way. */
 int mk_ctx_set_graphs(mk_ctx *ctx, int on);
+
+/* How the operators (mk_*_kbit) run their netlists on the NTT forms.
+ * MK_EXEC_LEVELS: one batched bootstrap + key-switch launch pair per netlist
+ * level (the cluster latency kernel for narrow levels).  MK_EXEC_PERSISTENT:
+ * one launch over every (gate, pair) of the netlist: CTAs take gates in the
+ * netlist's level order, wait (bounded, MK_ETIMEOUT through mk_sync) until
+ * the gate's input wires are ready (giving up when no gate of the launch
+ * finishes for the wait bound of mk_debug_fault), and run the gate's blind
+ * rotation and key switch, so a gate starts as soon as its own inputs exist
+ * instead of after the whole previous level.  MK_EXEC_AUTO (default): the
+ * level loop, which measured faster on every operator (their pairs advance
+ * in step, and the persistent launch switches keys one gate at a time).
+ * Results are identical.  No paper counterpart (Alg. 3-6 define the
+ * circuits, not their schedule). */
+enum { MK_EXEC_AUTO = 0, MK_EXEC_LEVELS = 1, MK_EXEC_PERSISTENT = 2 };
+int mk_ctx_set_circuit_exec(mk_ctx *ctx, int mode);
 
 /* Construction family of the operator netlists (same functions, same
  * quotient and remainder rules).  MK_CIRCUIT_ARRAY (default): the paper's

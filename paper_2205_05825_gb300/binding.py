@@ -80,6 +80,7 @@ _SIGS = {
     "mk_gates_lin": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_gate_lin": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, VP]),
     "mk_debug_fault": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64]),
+    "mk_ctx_set_circuit_exec": (ctypes.c_int, [VP, ctypes.c_int]),
     "mk_not": (ctypes.c_int, [VP, VP, VP, ctypes.c_size_t]),
     "mk_gates_noalloc": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
     "mk_stage_modswitch": (ctypes.c_int, [VP, VP, VP, VP, VP, ctypes.c_size_t]),
@@ -245,7 +246,13 @@ class Context:
         """Latency (cluster) kernel: "auto" (small launches), "on" or "off"."""
         self._check(self.L.mk_ctx_set_cluster(self.h, CLUSTER_MODES[mode]), "mk_ctx_set_cluster")
 
-    FAULTS = {"none": 0, "skip_key_step": 1, "skip_digit_tile": 2}
+    FAULTS = {"none": 0, "skip_key_step": 1, "skip_digit_tile": 2, "skip_wire_ready": 3}
+    CIRCUIT_EXEC = {"auto": 0, "levels": 1, "persistent": 2}
+
+    def set_circuit_exec(self, mode):
+        """Operators: "levels" (a launch pair per netlist level), "persistent"
+        (one launch over every gate and pair) or "auto"."""
+        self._check(self.L.mk_ctx_set_circuit_exec(self.h, self.CIRCUIT_EXEC[mode]), "mk_ctx_set_circuit_exec")
 
     def debug_fault(self, kind="none", arg=0, wait_ns=0):
         """Test hook of the bounded waits (mk_debug_fault): skip one key copy

@@ -156,7 +156,7 @@ struct KeyRing {
             if (st_globaltimer() - t0 > wait_ns) break;
         }
         *(volatile uint32_t *)&ctl->abort = 1;
-        atomicOr(status, 1u);
+        atomicOr(status, kStatusStaged);
         return false;
     }
 

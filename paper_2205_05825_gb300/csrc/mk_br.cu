@@ -6,6 +6,7 @@
 #include "mk_bootstrap.cuh"
 #include "mk_bootstrap_fft.cuh"
 #include "mk_bootstrap_split.cuh"
+#include "mk_netlist.cuh"
 #include "mk_bootstrap_staged.cuh"
 
 #ifndef MK_LOGN
@@ -64,3 +65,21 @@ cudaError_t MK_FN(const LaunchShape &S, const DeviceKeys &K, const GateDesc *des
 #endif
 }
 }  // namespace mk
+
+#if MK_VARIANT == 2 && MK_FIELD != 2
+// The persistent netlist kernel of this (ring dimension, field), with variant
+// 2's blind-rotation parameters.
+#define MK_NL_FN MK_CAT(launch_netlist_logn, MK_LOGN, _f, MK_FIELD, , )
+namespace mk {
+cudaError_t MK_NL_FN(const LaunchShape &S, const DeviceKeys &K, const NetlistArgs &A, uint32_t sm_count,
+                     cudaStream_t st) {
+#if MK_FIELD == 0
+    using F = br::FieldGold;
+#else
+    using F = br::FieldDual;
+#endif
+    return br::launch_netlist<F, MK_LOGN, kVariantNpf[2], kVariantMinBlocks[2], kVariantTwg[2] != 0, kVariantEpt[2]>(
+        S, K, A, sm_count, st);
+}
+}  // namespace mk
+#endif

@@ -279,6 +279,11 @@ struct CircuitPlan {
     uint32_t *d_pool = nullptr;
     uint32_t *d_ext = nullptr;
     int32_t *d_outs = nullptr;
+    // persistent execution: a ready word per pool row, {item counter, abort}
+    uint32_t *d_ready = nullptr;
+    uint32_t *d_ctl = nullptr;
+    uint32_t epoch = 0;
+    uint32_t levels = 0;
     // The level loop captured as a CUDA graph, and what it was captured with.
     cudaGraphExec_t graph = nullptr;
     int graph_form = -1, graph_variant = -1;
@@ -290,6 +295,8 @@ struct CircuitPlan {
         cudaFree(d_pool);
         cudaFree(d_ext);
         cudaFree(d_outs);
+        cudaFree(d_ready);
+        cudaFree(d_ctl);
     }
 };
 
@@ -327,6 +334,8 @@ struct mk_ctx {
     bool use_graphs = true;               // circuits replay their level loop as a CUDA graph
     int circuit_style = MK_CIRCUIT_ARRAY;  // netlist family of the operators
     int cluster_mode = MK_CLUSTER_AUTO;   // latency (cluster) kernel for small batches
+    int circuit_exec = MK_EXEC_AUTO;      // operators: one launch pair per level, or one persistent launch
+    int64_t debug_skip_item = -1;         // test hook of the persistent launch (mk_debug_fault)
     uint32_t sm_count = 0;
     cudaStream_t capture_stream = nullptr;  // non-default stream the graphs are captured on
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];

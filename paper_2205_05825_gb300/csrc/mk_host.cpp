@@ -438,6 +438,10 @@ int get_plan(mk_ctx *c, int op, uint32_t k, uint32_t pairs, CircuitPlan **out) {
     MK_CUDA(c, cudaMalloc(&plan->d_pool, (size_t)plan->n_wires * pairs * c->W() * 4));
     MK_CUDA(c, cudaMalloc(&plan->d_ext, (size_t)std::max<uint32_t>(plan->max_level, 1) * c->E() * 4));
     MK_CUDA(c, cudaMalloc(&plan->d_outs, outs.size() * sizeof(int32_t)));
+    MK_CUDA(c, cudaMalloc(&plan->d_ready, (size_t)plan->n_wires * pairs * sizeof(uint32_t)));
+    MK_CUDA(c, cudaMemset(plan->d_ready, 0, (size_t)plan->n_wires * pairs * sizeof(uint32_t)));
+    MK_CUDA(c, cudaMalloc(&plan->d_ctl, 4 * sizeof(uint32_t)));
+    plan->levels = L;
     MK_CUDA(c, cudaMemcpy(plan->d_desc, desc.data(), desc.size() * sizeof(GateDesc), cudaMemcpyHostToDevice));
     MK_CUDA(c, cudaMemcpy(plan->d_outs, outs.data(), outs.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     *out = plan.get();
@@ -495,12 +499,30 @@ int run_circuit(mk_ctx *c, int op, uint32_t k, const uint32_t *d_a, const uint32
     cudaError_t e = launch_circuit_consts(pl->d_pool, P, W, c->stream);
     if (e == cudaSuccess) e = launch_circuit_inputs(pl->d_pool, d_a, k, P, 2, W, c->stream);
     if (e == cudaSuccess) e = launch_circuit_inputs(pl->d_pool, d_b, k, P, 2 + k, W, c->stream);
+    // One persistent launch over every (gate, pair) item (NTT forms), or one
+    // launch pair per level.  AUTO takes the level loop: on these netlists
+    // every pair advances through the levels in step, so the persistent
+    // launch overlaps little that the level barriers hold back, and its
+    // per-gate key switch (each gate reads its own key-switch rows) costs more
+    // than the batched one (measured slower for every operator and width).
+    const uint32_t items = (uint32_t)pl->net.gates.size() * P;
+    const bool ntt_form = c->form == MK_FORM_NTT || c->form == MK_FORM_NTT2;
+    const bool persistent = ntt_form && c->circuit_exec == MK_EXEC_PERSISTENT;
+    bool replayed = false;
+    if (e == cudaSuccess && persistent) {
+        if (++pl->epoch == 0) ++pl->epoch;  // 0 marks rows never written
+        NetlistArgs A{pl->d_desc, items, pl->d_pool, (2 + pl->net.ka + pl->net.kb) * P, pl->d_ready, pl->epoch,
+                      pl->d_ctl, pl->d_ctl + 1, pl->d_ctl + 2, c->debug_skip_item};
+        e = cudaMemsetAsync(pl->d_ctl, 0, 3 * sizeof(uint32_t), c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, MK_KERNEL_BOOTSTRAP, [&] { return launch_netlist(S, K, A, c->sm_count, c->stream); });
+        replayed = true;
+    }
     // The level loop reads and writes only the plan's own buffers, so it is
     // captured once as a CUDA graph (per form, variant and key buffers) and
     // replayed; the tensor form (thousands of launches per level) and timed
     // runs launch directly.
-    bool replayed = false;
-    if (e == cudaSuccess && c->use_graphs && !c->timing && c->form != MK_FORM_TC) {
+    if (e == cudaSuccess && !replayed && c->use_graphs && !c->timing && c->form != MK_FORM_TC) {
         if (pl->graph && (pl->graph_form != c->form || pl->graph_variant != c->variant ||
                           pl->graph_cluster != S.cluster_max ||
                           std::memcmp(&pl->graph_keys, &K, sizeof(K)) != 0)) {
@@ -705,10 +727,11 @@ int mk_ctx_set_cluster(mk_ctx *c, int mode) {
 
 int mk_debug_fault(mk_ctx *c, int kind, int64_t arg, uint64_t wait_ns) {
     if (!c) return MK_EINVAL;
-    if (kind != MK_FAULT_NONE && kind != MK_FAULT_SKIP_KEY_STEP && kind != MK_FAULT_SKIP_DIGIT_TILE)
+    if (kind != MK_FAULT_NONE && kind != MK_FAULT_SKIP_KEY_STEP && kind != MK_FAULT_SKIP_DIGIT_TILE &&
+        kind != MK_FAULT_SKIP_WIRE_READY)
         return fail(c, MK_EINVAL, "unknown fault kind");
-    if ((kind == MK_FAULT_SKIP_KEY_STEP || kind == MK_FAULT_SKIP_DIGIT_TILE) && arg < 0)
-        return fail(c, MK_EINVAL, "fault argument must be >= 0");
+    if (kind != MK_FAULT_NONE && arg < 0) return fail(c, MK_EINVAL, "fault argument must be >= 0");
+    c->debug_skip_item = kind == MK_FAULT_SKIP_WIRE_READY ? arg : -1;
     if (kind == MK_FAULT_SKIP_DIGIT_TILE && c->device < 0) return fail(c, MK_EDEVICE, "host-only context");
     c->wait_ns = wait_ns ? wait_ns : 1000000000ull;
     c->debug_skip_key_step = kind == MK_FAULT_SKIP_KEY_STEP ? arg : -1;
@@ -723,6 +746,14 @@ int mk_debug_fault(mk_ctx *c, int kind, int64_t arg, uint64_t wait_ns) {
             cudaGraphExecDestroy(kv.second->graph);
             kv.second->graph = nullptr;
         }
+    return MK_OK;
+}
+
+int mk_ctx_set_circuit_exec(mk_ctx *c, int mode) {
+    if (!c) return MK_EINVAL;
+    if (mode != MK_EXEC_AUTO && mode != MK_EXEC_LEVELS && mode != MK_EXEC_PERSISTENT)
+        return fail(c, MK_EINVAL, "circuit execution must be MK_EXEC_AUTO, _LEVELS or _PERSISTENT");
+    c->circuit_exec = mode;
     return MK_OK;
 }
 
@@ -867,12 +898,14 @@ int mk_sync(mk_ctx *c) {
         MK_CUDA(c, tc05_error(&timeout, true));
         if (timeout) return fail(c, MK_ETIMEOUT, "a bounded wait of the tensor-core product kernel gave up");
     }
-    if (c->d_status) {  // the staged blind rotation's bounded waits for its key copies
+    if (c->d_status) {  // the staged blind rotation's and the persistent operator launch's bounded waits
         uint32_t st = 0;
         MK_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
         if (st) {
             MK_CUDA(c, cudaMemset(c->d_status, 0, sizeof(st)));
-            return fail(c, MK_ETIMEOUT, "a bounded wait of the staged blind rotation for a key copy gave up");
+            if (st & kStatusStaged)
+                return fail(c, MK_ETIMEOUT, "a bounded wait of the staged blind rotation for a key copy gave up");
+            return fail(c, MK_ETIMEOUT, "the persistent operator launch made no progress within its bound");
         }
     }
     return MK_OK;

@@ -46,13 +46,16 @@ struct DeviceKeys {
     // the wave workspace holds tc_ws_gates gates (a multiple of 64).
     void *tc_ws;
     uint32_t tc_ws_gates;
-    // The context's status word (device): kernels with bounded waits set bit 0
-    // when a wait runs out; mk_sync reports it as MK_ETIMEOUT and clears it.
+    // The context's status word (device): a kernel whose bounded wait ran out
+    // sets its bit (kStatusStaged, kStatusNetlist); mk_sync reports it as
+    // MK_ETIMEOUT and clears it.
     uint32_t *status;
     // MK_FORM_NTT2: per-prime twiddles [2 directions][2 primes][N] uint2
     // {w, w'} for the split-prime kernel (nullptr for the other forms).
     const void *tw_split;
 };
+
+constexpr uint32_t kStatusStaged = 1u, kStatusNetlist = 2u;
 
 struct LaunchShape {
     uint32_t n, N, logN, k, d, bg_bit, ks_bit, t;
@@ -138,6 +141,32 @@ MK_DECLARE_CLUSTER(8, 0)
 MK_DECLARE_CLUSTER(8, 1)
 MK_DECLARE_CLUSTER(10, 0)
 MK_DECLARE_CLUSTER(10, 1)
+
+// A whole operator netlist in one persistent launch (mk_netlist.cuh): every
+// (gate, pair) item of the plan, taken by CTAs in topological order, each
+// waiting for its input rows to be marked ready.  NTT forms only; built in
+// the variant-2 translation unit of each (ring dimension, field).
+struct NetlistArgs {
+    const GateDesc *desc;  // items in topological order; ia, ib, out are pool rows
+    uint32_t count;        // items
+    uint32_t *pool;        // [rows][k n + 1] ciphertext rows
+    uint32_t input_rows;   // rows below this (inputs and constants) are ready from the start
+    uint32_t *ready;       // [rows]: the epoch of the call that wrote the row
+    uint32_t epoch;        // this call's epoch (never 0)
+    uint32_t *next;        // item counter (0 at launch)
+    uint32_t *abort;       // set when some wait ran out (0 at launch)
+    uint32_t *done;        // items finished (0 at launch): the progress the waits watch
+    int64_t skip_item;     // test hook: this item never marks its output ready (-1: none)
+};
+#define MK_DECLARE_NETLIST(LOGN, F)                                                                          \
+    cudaError_t launch_netlist_logn##LOGN##_f##F(const LaunchShape &S, const DeviceKeys &K, const NetlistArgs &A, \
+                                                 uint32_t sm_count, cudaStream_t st);
+MK_DECLARE_NETLIST(8, 0)
+MK_DECLARE_NETLIST(8, 1)
+MK_DECLARE_NETLIST(10, 0)
+MK_DECLARE_NETLIST(10, 1)
+cudaError_t launch_netlist(const LaunchShape &S, const DeviceKeys &K, const NetlistArgs &A, uint32_t sm_count,
+                           cudaStream_t st);
 
 // MK_FORM_TC (mk_tensor.cu): the blind rotation of a batch as a wave of
 // tensor-core Toeplitz products.  Same arguments as the launchers above;

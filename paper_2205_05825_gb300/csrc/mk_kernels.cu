@@ -410,6 +410,15 @@ cudaError_t launch_blind_rotate_ntt(const LaunchShape &S, const DeviceKeys &K, c
     return f(S, K, nullptr, nullptr, nullptr, abar, max_steps, nullptr, acc, count, st);
 }
 
+cudaError_t launch_netlist(const LaunchShape &S, const DeviceKeys &K, const NetlistArgs &A, uint32_t sm_count,
+                           cudaStream_t st) {
+    if (S.form == MK_FORM_NTT && S.logN == 8) return launch_netlist_logn8_f0(S, K, A, sm_count, st);
+    if (S.form == MK_FORM_NTT && S.logN == 10) return launch_netlist_logn10_f0(S, K, A, sm_count, st);
+    if (S.form == MK_FORM_NTT2 && S.logN == 8) return launch_netlist_logn8_f1(S, K, A, sm_count, st);
+    if (S.form == MK_FORM_NTT2 && S.logN == 10) return launch_netlist_logn10_f1(S, K, A, sm_count, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_modswitch(const LaunchShape &S, const GateDesc *desc, const uint32_t *ct_a,
                              const uint32_t *ct_b, uint32_t *abar, uint32_t count, cudaStream_t st) {
     if (count == 0) return cudaSuccess;

@@ -194,3 +194,76 @@ def test_toy_graph_replay_matches_direct_launches(toy, op):
     assert np.array_equal(g1, direct) and np.array_equal(g2, direct) and np.array_equal(timed_, direct)
     assert np.array_equal(other_form, direct)
     _check(P, keys, op, 4, a, b, g1)
+
+
+@pytest.mark.parametrize("style", ["array", "shallow"])
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_toy_persistent_launch_bit_exact(toy, op, style):
+    """The whole netlist in one persistent launch (gates waiting for their own
+    input wires, no level barrier) gives the level loop's ciphertexts and the
+    oracle's, word for word."""
+    from oracle import circuits as C
+    P, keys, ctx = toy
+    a = np.array([-8, 5, -1, 7], np.int64)
+    b = np.array([3, -7, 2, -8], np.int64)
+    ca, cb = _encrypt_operands(P, keys, a, b, 4, 730)
+    ctx.set_circuit_style(style)
+    try:
+        ctx.set_circuit_exec("persistent")
+        got = _run(ctx, op, 4, ca, cb)
+        got2 = _run(ctx, op, 4, ca, cb)  # a second call: new epoch, same plan
+        ctx.set_circuit_exec("levels")
+        lev = _run(ctx, op, 4, ca, cb)
+        ctx.sync()
+    finally:
+        ctx.set_circuit_exec("auto")
+        ctx.set_circuit_style("array")
+    assert np.array_equal(got, lev) and np.array_equal(got2, lev)
+    ref = C.eval_encrypted(P, keys, C.build(op, 4, style), ca[:2], cb[:2])
+    assert np.array_equal(got[:2], ref)
+
+
+@pytest.mark.parametrize("op,pairs", [("add", 64), ("mul", 16)])
+def test_full_k2_persistent_launch_equals_levels(full2, op, pairs):
+    """Full size: the persistent launch and the level loop give the same
+    ciphertexts, which decrypt to the native results."""
+    from paper_2205_05825_gb300 import workloads as W
+    P, keys, ctx = full2
+    a, b = W.random_operands(8, pairs, config_id=34)
+    ca, cb = _encrypt_operands(P, keys, a, b, 8, 770)
+    try:
+        ctx.set_circuit_exec("persistent")
+        got = _run(ctx, op, 8, ca, cb)
+        ctx.set_circuit_exec("levels")
+        lev = _run(ctx, op, 8, ca, cb)
+        ctx.sync()
+    finally:
+        ctx.set_circuit_exec("auto")
+    assert np.array_equal(got, lev)
+    _check(P, keys, op, 8, a, b, got)
+
+
+def test_toy_persistent_launch_wait_runs_out(toy):
+    """A wire that is never marked ready (test hook): the gates reading it
+    give up after the bound, mk_sync reports MK_ETIMEOUT once, and the next
+    call on the same context is bit-exact again."""
+    from oracle import circuits as C
+    from paper_2205_05825_gb300 import binding as B
+    P, keys, ctx = toy
+    a = np.array([-8, 5], np.int64)
+    b = np.array([3, -7], np.int64)
+    ca, cb = _encrypt_operands(P, keys, a, b, 4, 740)
+    try:
+        ctx.set_circuit_exec("persistent")
+        ctx.debug_fault("skip_wire_ready", 0, 50_000_000)  # item 0: a first-level gate of the adder
+        _run(ctx, "add", 4, ca, cb)
+        with pytest.raises(B.MkError, match="MK_ETIMEOUT"):
+            ctx.sync()
+        ctx.sync()
+        ctx.debug_fault("none")
+        got = _run(ctx, "add", 4, ca, cb)
+        ctx.sync()
+    finally:
+        ctx.debug_fault("none")
+        ctx.set_circuit_exec("auto")
+    assert np.array_equal(got, C.eval_encrypted(P, keys, C.build("add", 4), ca, cb))
