@@ -271,7 +271,7 @@ __device__ __forceinline__ void group_sync(int bar_id, int nthreads) {
 // omits the 1/N factor (the keys carry it).  Between passes the elements move
 // through padded shared memory (one pad word every 16 keeps each 64-bit warp
 // access at the 2-wavefront minimum).
-__device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }
+__host__ __device__ constexpr int pidx(int j) { return j + (j >> 4); }
 
 // Twiddle tables are stored with one pad entry every 4, so the stride-2 and
 // stride-4 twiddle reads of the late stages hit distinct banks.
@@ -353,14 +353,79 @@ struct Ntt {
         group_sync(bar_id, T);
     }
 
+    // The same exchange with both layouts known at compile time.  jbase's
+    // bits and c << LO are disjoint, so their sum carries nothing and
+    // pidx(jbase | c << LO) = pidx(jbase) + pidx(c << LO): one address per
+    // thread and layout, every element at an immediate offset from it.
+    template <int NP, int LOF, int LOT>
+    __device__ static __forceinline__ void exchange_ct(E (&x)[NP][EPT], int tid, E *buf, int bar_id) {
+        const int bf = jbase<SB>(tid, LOF);
+        E *wb = buf + pidx(bf);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < EPT; ++c) wb[p * PN + pidx(c << LOF)] = x[p][c];
+        group_sync(bar_id, T);
+        const int bt = jbase<SB>(tid, LOT);
+        const E *rb = buf + pidx(bt);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < EPT; ++c) x[p][c] = rb[p * PN + pidx(c << LOT)];
+        group_sync(bar_id, T);
+    }
+
+    // Layout (LO) of pass q of the forward / inverse transform, as the pass
+    // loops below compute it.
+    __host__ __device__ static constexpr int pass_lo(bool fwd, int q) {
+        return fwd ? ((LOGN - 1 - SB * q) >= SB - 1 ? (LOGN - 1 - SB * q) - (SB - 1) : 0)
+                   : ((SB * q < LOGN - SB) ? SB * q : LOGN - SB);
+    }
+    static constexpr int NPASS = (LOGN + SB - 1) / SB;
+
+    // Exchange before pass q (1 <= q < NPASS) with compile-time layouts for
+    // the passes of a transform of up to five passes; runtime layouts beyond.
+    template <int NP, bool FWD>
+    __device__ static __forceinline__ void exchange_pass(E (&x)[NP][EPT], int tid, E *buf, int q, int LOf, int LOt,
+                                                         int bar_id) {
+        constexpr int L0 = pass_lo(FWD, 0), L1 = pass_lo(FWD, 1), L2 = pass_lo(FWD, 2), L3 = pass_lo(FWD, 3),
+                      L4 = pass_lo(FWD, 4);
+        if constexpr (L0 != L1) {
+            if (q == 1) {
+                exchange_ct<NP, L0, L1>(x, tid, buf, bar_id);
+                return;
+            }
+        }
+        if constexpr (NPASS > 2 && L1 != L2) {
+            if (q == 2) {
+                exchange_ct<NP, L1, L2>(x, tid, buf, bar_id);
+                return;
+            }
+        }
+        if constexpr (NPASS > 3 && L2 != L3) {
+            if (q == 3) {
+                exchange_ct<NP, L2, L3>(x, tid, buf, bar_id);
+                return;
+            }
+        }
+        if constexpr (NPASS > 4 && L3 != L4) {
+            if (q == 4) {
+                exchange_ct<NP, L3, L4>(x, tid, buf, bar_id);
+                return;
+            }
+        }
+        exchange<NP>(x, tid, buf, LOf, LOt, bar_id);
+    }
+
     // natural (layout logN-SB) -> bit-reversed (layout 0)
     template <int NP>
     __device__ static __forceinline__ void forward(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf, int bar_id = 0) {
         int prev = LOGN - SB;
+        int q = 0;
 #pragma unroll 1
-        for (int hi = LOGN - 1; hi >= 0; hi -= SB) {
+        for (int hi = LOGN - 1; hi >= 0; hi -= SB, ++q) {
             const int LO = hi >= SB - 1 ? hi - (SB - 1) : 0;
-            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO, bar_id);
+            if (LO != prev) exchange_pass<NP, true>(x, tid, buf, q, prev, LO, bar_id);
             const int jb = jbase<SB>(tid, LO);
             if constexpr (SB == 3) {
                 if (hi - LO == 2) fwd_stage<NP, 4>(x, jb, LO, LO + 2, tw);
@@ -375,11 +440,12 @@ struct Ntt {
     template <int NP>
     __device__ static __forceinline__ void inverse(E (&x)[NP][EPT], int tid, const Tw *tw, E *buf, int bar_id = 0) {
         int prev = 0;
+        int q = 0;
 #pragma unroll 1
-        for (int lo = 0; lo < LOGN; lo += SB) {
+        for (int lo = 0; lo < LOGN; lo += SB, ++q) {
             const int hi = (lo + SB - 1 < LOGN - 1) ? lo + SB - 1 : LOGN - 1;
             const int LO = (lo < LOGN - SB) ? lo : LOGN - SB;
-            if (LO != prev) exchange<NP>(x, tid, buf, prev, LO, bar_id);
+            if (LO != prev) exchange_pass<NP, false>(x, tid, buf, q, prev, LO, bar_id);
             const int jb = jbase<SB>(tid, LO);
             if (lo == LO) inv_stage<NP, 1>(x, jb, LO, LO, tw);
             if (lo <= LO + 1 && hi >= LO + 1) inv_stage<NP, 2>(x, jb, LO, LO + 1, tw);
