@@ -47,8 +47,9 @@ WORKLOAD = "full-size MK gate bootstrap, k=2 parties, n=560, N=1024, 4096 random
 
 # ----------------------------------------------------------------------------- distributed helpers
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    """(rank, world size, local rank): the library's replica helper."""
+    from paper_2205_05825_gb300.replicas import dist_env as env
+    return env()
 
 
 def shard_seed(config_id, rank):
