@@ -22,7 +22,7 @@ bounded summaries of the other configurations -- the precision sweep
 application (shallow netlists), the k-bit operators (8-bit throughput,
 16-bit single-pair latency, both netlist families) and the serving loop
 (k = 4, 16-bit requests, a closed batch and Poisson arrivals at 0.5 and 0.9
-of its capacity).  --sweep, --regression and --operators run the full
+of its capacity, with the array and the shallow netlists).  --sweep, --regression and --operators run the full
 versions; --no-extras leaves the summaries out.
 """
 import argparse
@@ -262,8 +262,8 @@ def run_operators(dev_index, full=False):
     with full=True).  Default (bounded): throughput of 8-bit add and multiply
     over 64 pairs (array netlists), and the latency of one pair of each
     16-bit operator with both netlist families.  full=True: the config-3
-    table, every operator at 8 and 16 bits over 256 pairs, k = 2 and 4, both
-    families.  Wall-clock seconds with the device synchronised on both sides;
+    table, every operator at 8 and 16 bits over 256 pairs: k = 2 with both
+    families, k = 4 with the array family.  Wall-clock seconds with the device synchronised on both sides;
     every output decrypted against native two's-complement arithmetic."""
     import torch
 
@@ -271,7 +271,7 @@ def run_operators(dev_index, full=False):
     from paper_2205_05825_gb300 import workloads as W
     dev = "cuda:%d" % dev_index
     if full:
-        cases = [(k, style, op, bits, 256) for k in (2, 4) for style in ("array", "shallow")
+        cases = [(k, style, op, bits, 256) for k, style in ((2, "array"), (2, "shallow"), (4, "array"))
                  for bits in (8, 16) for op in ("add", "sub", "mul", "div")]
     else:
         cases = ([(2, "array", op, 8, 64) for op in ("add", "mul")] +
@@ -672,8 +672,9 @@ def run_ours(args):
     serving = None
     if extras:
         from paper_2205_05825_gb300.serving import run_serving
-        serving = guarded(lambda: run_serving(parties=4, bits=16, capacity_requests=48, requests=24,
-                                              loads=(0.5, 0.9), device=dev_index))
+        serving = {style: guarded(lambda style=style: run_serving(
+                       parties=4, bits=16, capacity_requests=48, requests=24, loads=(0.5, 0.9), device=dev_index,
+                       circuit_style=style)) for style in ("array", "shallow")}
 
     # roofline of the dominant kernel (blind rotation), live from the timed region
     avg_br_ms = br_ms / max(br_n, 1)
@@ -832,8 +833,8 @@ def main():
     ap.add_argument("--regression", action="store_true",
                     help="also time the encrypted linear regression (Algorithms 7 and 8) at k = 2, full size")
     ap.add_argument("--operators", action="store_true",
-                    help="also time the config-3 operator table (every operator, 8 and 16 bits, 256 pairs, "
-                         "k = 2 and 4, both netlist families)")
+                    help="also time the config-3 operator table (every operator, 8 and 16 bits, 256 pairs; "
+                         "k = 2 with both netlist families, k = 4 with the array family)")
     ap.add_argument("--no-extras", action="store_true",
                     help="leave out the bounded sweep, regression, operator and serving summaries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
