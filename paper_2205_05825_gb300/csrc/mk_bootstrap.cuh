@@ -269,9 +269,14 @@ __device__ __forceinline__ void group_sync(int bar_id, int nthreads) {
 // layout LO = logN-SB (coefficient tid + T*c), output bit-reversed order in
 // layout LO = 0 (index EPT*tid + c).  Inverse (Gentleman-Sande) goes back, and
 // omits the 1/N factor (the keys carry it).  Between passes the elements move
-// through padded shared memory (one pad word every 16 keeps each 64-bit warp
-// access at the 2-wavefront minimum).
-__host__ __device__ constexpr int pidx(int j) { return j + (j >> 4); }
+// through padded shared memory, two pad elements after every 16: measured
+// on GB300 (ncu, a 608-gate launch of the two-prime form), the exchanges'
+// bank conflicts fell from 1.40 G wavefronts with one pad element per 16 to
+// 0.01 G, and the launch from 64.5 to 61.4 ms.  The padding adds a fixed
+// offset per index bit, which the compile-time exchange relies on.
+__host__ __device__ constexpr int pidx(int j) { return j + 2 * (j >> 4); }
+// Length of one padded polynomial of n elements in an exchange buffer.
+__host__ __device__ constexpr int padded_len(int n) { return n + n / 8; }
 
 // Twiddle tables are stored with one pad entry every 4, so the stride-2 and
 // stride-4 twiddle reads of the late stages hit distinct banks.
@@ -298,7 +303,7 @@ struct Ntt {
     static constexpr int SB = log2_ept(EPT);
     static_assert(EPT == 8 || EPT == 4, "8 or 4 elements per thread");
     static constexpr int T = N / EPT;
-    static constexpr int PN = N + N / 16;  // padded polynomial stride in xbuf
+    static constexpr int PN = padded_len(N);  // padded polynomial stride in xbuf
 
     // Forward stage at bit b (distance 2^b) inside a pass with element bits
     // [LO, LO+SB): element pairs (c, c + D), D = 2^(b - LO).  The pair's
@@ -497,7 +502,7 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t k, uint32_t n) {
     L.twi = L.twf + tw_bytes;
     L.xbuf = L.twi + tw_bytes;
     // exchange buffer for NPF forward or 2 inverse transforms at once
-    L.acc = L.xbuf + sizeof(E) * (NPF > 2 ? NPF : 2) * (N + N / 16);
+    L.acc = L.xbuf + sizeof(E) * (NPF > 2 ? NPF : 2) * padded_len(N);
     L.abar = L.acc + sizeof(uint32_t) * (k + 1) * N;
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
     return L;

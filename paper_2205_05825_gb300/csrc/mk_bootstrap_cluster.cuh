@@ -46,7 +46,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(uint32_t k, uint32_t n) 
     ClusterLayout L;
     L.acc = 0;
     L.xbuf = L.acc + sizeof(uint32_t) * N;
-    L.vbuf = L.xbuf + sizeof(E) * 3 * (N + N / 16);  // three padded polynomials per forward pass
+    L.vbuf = L.xbuf + sizeof(E) * 3 * padded_len(N);  // three padded polynomials per forward pass
     L.wbuf = L.vbuf + sizeof(E) * (k + 1) * N;  // CTA 0: the k+1 shares of v
     L.abar = L.wbuf + sizeof(E) * 3 * N;        // CTA 0 and CTA i: NTT(w_l)
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));

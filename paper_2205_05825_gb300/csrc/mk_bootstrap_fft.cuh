@@ -170,7 +170,7 @@ __host__ __device__ inline FftSmem fft_smem_layout(uint32_t k, uint32_t n) {
     L.twi = L.twf + sizeof(double2) * (M + M / 4);
     L.theta = L.twi + sizeof(double2) * (M + M / 4);
     L.xbuf = L.theta + sizeof(double2) * M;
-    L.acc = L.xbuf + sizeof(double2) * (M + M / 16);
+    L.acc = L.xbuf + sizeof(double2) * padded_len(M);
     L.abar = L.acc + sizeof(uint32_t) * (k + 1) * 2 * M;
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
     return L;

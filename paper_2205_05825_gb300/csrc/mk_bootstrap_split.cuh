@@ -30,7 +30,7 @@ struct PrimeOne {
 template <int LOGN>
 struct NttOne {
     static constexpr int N = 1 << LOGN, EPT = 8, SB = 3, T = N / EPT;
-    static constexpr int PN = N + N / 16;  // padded polynomial stride in the exchange buffer
+    static constexpr int PN = padded_len(N);  // padded polynomial stride in the exchange buffer
 
     // Harvey/Shoup butterflies: forward inputs and outputs in [0, 4p); inverse in [0, 2p).
     __device__ static __forceinline__ void fwd(uint32_t &X, uint32_t &Y, const uint2 &W, const PrimeOne &P) {
@@ -144,7 +144,7 @@ template <int LOGN, int NPF>
 __host__ __device__ inline SplitLayout split_layout(uint32_t k, uint32_t n) {
     constexpr size_t N = (size_t)1 << LOGN;
     SplitLayout L;
-    L.xwords = (NPF > 2 ? NPF : 2) * (N + N / 16);  // one prime's exchange buffer, in words
+    L.xwords = (NPF > 2 ? NPF : 2) * padded_len(N);  // one prime's exchange buffer, in words
     L.xbuf = 0;
     L.acc = L.xbuf + 2 * sizeof(uint32_t) * L.xwords;
     L.vbuf = L.acc + sizeof(uint32_t) * (k + 1) * N;

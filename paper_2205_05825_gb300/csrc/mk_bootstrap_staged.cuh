@@ -112,7 +112,7 @@ __host__ __device__ inline StagedLayout staged_layout(uint32_t k, uint32_t n, in
     L.ctl = L.keyF + sizeof(E) * 6 * N;
     L.group0 = (L.ctl + sizeof(StagedCtl) + 127) & ~size_t(127);
     L.xbuf = 0;  // offsets within a group
-    L.acc = L.xbuf + sizeof(E) * (NPF > 2 ? NPF : 2) * (N + N / 16);
+    L.acc = L.xbuf + sizeof(E) * (NPF > 2 ? NPF : 2) * padded_len(N);
     L.abar = L.acc + sizeof(uint32_t) * (k + 1) * N;
     L.group_bytes = (L.abar + sizeof(uint16_t) * (k * n + 1) + 127) & ~size_t(127);
     L.total = L.group0 + (size_t)G * L.group_bytes;

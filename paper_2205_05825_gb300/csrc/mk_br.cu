@@ -1,6 +1,6 @@
 // Blind-rotation instantiation for one (ring dimension, field, variant),
 // chosen by the build with -DMK_LOGN=<log2 N> -DMK_FIELD=<0|1>
-// -DMK_VARIANT=<v>; field 0 = Goldilocks (MK_FORM_NTT), 1 = two 30-bit primes
+// -DMK_VARIANT=<v>; field 0 = Goldilocks (MK_FORM_NTT), 1 = two 28-bit primes
 // (MK_FORM_NTT2), 2 = FP64 FFT (MK_FORM_FFT, one variant); the variant table
 // is in mk_internal.h.
 #include "mk_bootstrap.cuh"
