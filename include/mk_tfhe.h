@@ -114,14 +114,13 @@ int mk_ctx_get_form(const mk_ctx *ctx, int *form);
 int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
 
 /* Latency (cluster) form of the NTT blind rotation: one thread-block cluster
- * of k+1 CTAs per gate, CTA j owning accumulator polynomial j, so a gate's
- * CMux chain runs about (k+2)/2 times faster while the GPU has SMs to spare.
- * MK_CLUSTER_AUTO (default) uses it for launches of at most
- * SM count / (k+1) gates for k <= 2 and 2 * SM count / (k+1) for k >= 3
- * (50, 60 and 38 gates at k = 2, 4 and 7 on 152 SMs); _ON for every
- * launch, _OFF never.  Only the
- * NTT forms with k <= 7; results are bit-identical either way.  No paper
- * counterpart: a scheduling choice. */
+ * of k+1 CTAs per gate, CTA j owning accumulator polynomial j, so one gate
+ * runs about k/2 times faster than in the batched kernel while the GPU has
+ * SMs to spare.  MK_CLUSTER_AUTO (default) uses it for launches of at most
+ * max(1, floor(k/2)) waves of gates, a wave being the clusters the device
+ * can hold at once (queried when the keys are laid out for the form); _ON
+ * for every launch, _OFF never.  Only the NTT forms with k <= 7; results are
+ * bit-identical either way.  No paper counterpart: a scheduling choice. */
 enum { MK_CLUSTER_AUTO = 0, MK_CLUSTER_OFF = 1, MK_CLUSTER_ON = 2 };
 int mk_ctx_set_cluster(mk_ctx *ctx, int mode);
 
@@ -132,8 +131,8 @@ int mk_ctx_set_cluster(mk_ctx *ctx, int mode);
  * work, lets its own copies and tensor-core operations finish, and returns
  * without its outputs; the next mk_sync reports MK_ETIMEOUT, and the context
  * stays usable.  kind MK_FAULT_SKIP_KEY_STEP: until the next call, the staged
- * kernel never copies the key entry of CMux step `arg` (0-based), so the
- * waits for it run out.  kind MK_FAULT_SKIP_DIGIT_TILE: in the next tcgen05
+ * kernel and the cluster latency kernel never copy the key entry of CMux step
+ * `arg` (0-based), so the waits for it run out.  kind MK_FAULT_SKIP_DIGIT_TILE: in the next tcgen05
  * launch, the first CTA that reaches its digit tile `arg` does not load it
  * (one shot).  kind MK_FAULT_SKIP_WIRE_READY: until the next call, the
  * persistent operator launch never marks the output of its work item `arg`

@@ -28,7 +28,7 @@ BR_INSTANCES = [(logn, f, v) for logn in (8, 10) for f in (0, 1) for v in range(
 BRC_SOURCE = "mk_brc.cu"
 BRC_INSTANCES = [(logn, f) for logn in (8, 10) for f in (0, 1)]
 CPP_SOURCES = ["mk_host.cpp", "mk_circuits.cpp", "mk_server.cpp"]
-HEADERS = ["mk_internal.h", "mk_ctx.h", "mk_bootstrap.cuh", "mk_bootstrap_fft.cuh", "mk_bootstrap_cluster.cuh",
+HEADERS = ["mk_internal.h", "mk_ctx.h", "mk_bootstrap.cuh", "mk_bulk.cuh", "mk_bootstrap_fft.cuh", "mk_bootstrap_cluster.cuh",
            "mk_bootstrap_staged.cuh", "mk_bootstrap_split.cuh", "mk_netlist.cuh",
            BR_SOURCE, BRC_SOURCE]
 

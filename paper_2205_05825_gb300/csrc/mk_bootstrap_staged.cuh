@@ -34,58 +34,10 @@
 // writing outputs.  The host reports the status as MK_ETIMEOUT.
 #pragma once
 #include "mk_bootstrap.cuh"
+#include "mk_bulk.cuh"
 
 namespace mk {
 namespace br {
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t st_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void st_mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool st_mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ uint64_t st_globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
-    return t;
-}
-
-// Order this thread's (and, through the synchronisation that preceded it,
-// the CTA's) generic-proxy accesses of shared memory before later async-proxy
-// (bulk copy) writes.
-__device__ __forceinline__ void st_fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-// Issue a bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
-// aligned) from global into this CTA's shared memory; the mbarrier `bar`
-// expects the bytes and completes its phase when they have landed.
-__device__ __forceinline__ void st_bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t st_atom_add_acqrel(uint32_t addr, uint32_t v) {
-    uint32_t old;
-    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;\n" : "=r"(old) : "r"(addr), "r"(v) : "memory");
-    return old;
-}
 
 // ------------------------------------------------------------ shared-memory layout
 // [D buffer: 3 N][F buffer: 6 N] elements, the control block, then per group

@@ -337,6 +337,7 @@ struct mk_ctx {
     int circuit_exec = MK_EXEC_AUTO;      // operators: one launch pair per level, or one persistent launch
     int64_t debug_skip_item = -1;         // test hook of the persistent launch (mk_debug_fault)
     uint32_t sm_count = 0;
+    uint32_t cluster_cap = 0;  // resident clusters of the latency form (for the keys' form; 0: unknown)
     cudaStream_t capture_stream = nullptr;  // non-default stream the graphs are captured on
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
     std::vector<cudaEvent_t> ev_pool;
@@ -348,13 +349,18 @@ struct mk_ctx {
     size_t bk_words() const { return (size_t)P.n * 3 * P.d * P.N; }
     size_t ks_words() const { return (size_t)P.N * P.t * ((1u << P.ks_bit) - 1) * (P.n + 1); }
     LaunchShape shape() const {
-        // AUTO: the cluster kernel while the launch's clusters need at most one
-        // CTA per SM (k <= 2) or two (k >= 3, where a gate's chain shortens
-        // more); beyond that the batched kernel's throughput wins.  Measured
-        // crossover on GB300: k = 2 at ~50 gates, k = 4 above 50, k = 7 above 30.
-        const uint32_t cmax = cluster_mode == MK_CLUSTER_ON ? 0xFFFFFFFFu
+        // AUTO: the cluster kernel while the launch's gates fit in max(1,
+        // floor(k/2)) waves of resident clusters (cluster_cap, queried from
+        // the device for the form's kernel); beyond that the batched kernel's
+        // throughput wins.  One gate runs about k/2 times faster in the
+        // cluster form (GB300: 22.6 vs 31.3 ms at k = 2, 47.3 vs 99.0 at
+        // k = 4, 84.8 vs 306 at k = 7), and the measured crossovers sit at
+        // one, two and three waves.  Without a capacity: SM count / (k + 1).
+        const uint32_t waves = P.k >= 4 ? P.k / 2 : 1u;
+        const uint32_t cmax = cluster_mode == MK_CLUSTER_ON    ? 0xFFFFFFFFu
                               : cluster_mode == MK_CLUSTER_OFF ? 0u
-                                                               : (P.k <= 2 ? 1u : 2u) * sm_count / (P.k + 1);
+                              : cluster_cap                    ? waves * cluster_cap
+                                                               : sm_count / (P.k + 1);
         return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form, cmax, wait_ns,
                            debug_skip_key_step};
     }

@@ -340,6 +340,8 @@ int ensure_device_keys(mk_ctx *c) {
     for (uint32_t i = 0; i < k; ++i)
         MK_CUDA(c, cudaMemcpy(c->d_ks + (size_t)i * c->ks_words(), c->party[i].ks.data(), c->ks_words() * 4,
                               cudaMemcpyHostToDevice));
+    c->cluster_cap = (uint32_t)cluster_capacity(c->shape());
+    (void)cudaGetLastError();  // a shape the device cannot host only leaves the capacity at 0
     c->dev_keys_valid = true;
     return MK_OK;
 }
@@ -898,13 +900,15 @@ int mk_sync(mk_ctx *c) {
         MK_CUDA(c, tc05_error(&timeout, true));
         if (timeout) return fail(c, MK_ETIMEOUT, "a bounded wait of the tensor-core product kernel gave up");
     }
-    if (c->d_status) {  // the staged blind rotation's and the persistent operator launch's bounded waits
+    if (c->d_status) {  // bounded waits of the staged and cluster blind rotations and the persistent operator launch
         uint32_t st = 0;
         MK_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
         if (st) {
             MK_CUDA(c, cudaMemset(c->d_status, 0, sizeof(st)));
             if (st & kStatusStaged)
                 return fail(c, MK_ETIMEOUT, "a bounded wait of the staged blind rotation for a key copy gave up");
+            if (st & kStatusCluster)
+                return fail(c, MK_ETIMEOUT, "a bounded wait of the cluster blind rotation for a key copy gave up");
             return fail(c, MK_ETIMEOUT, "the persistent operator launch made no progress within its bound");
         }
     }

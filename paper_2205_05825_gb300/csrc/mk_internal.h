@@ -47,7 +47,7 @@ struct DeviceKeys {
     void *tc_ws;
     uint32_t tc_ws_gates;
     // The context's status word (device): a kernel whose bounded wait ran out
-    // sets its bit (kStatusStaged, kStatusNetlist); mk_sync reports it as
+    // sets its bit (kStatusStaged, kStatusNetlist, kStatusCluster); mk_sync reports it as
     // MK_ETIMEOUT and clears it.
     uint32_t *status;
     // MK_FORM_NTT2: per-prime twiddles [2 directions][2 primes][N] uint2
@@ -55,7 +55,7 @@ struct DeviceKeys {
     const void *tw_split;
 };
 
-constexpr uint32_t kStatusStaged = 1u, kStatusNetlist = 2u;
+constexpr uint32_t kStatusStaged = 1u, kStatusNetlist = 2u, kStatusCluster = 4u;
 
 struct LaunchShape {
     uint32_t n, N, logN, k, d, bg_bit, ks_bit, t;
@@ -70,6 +70,10 @@ struct LaunchShape {
     uint64_t wait_ns;
     int64_t skip_key_step;
 };
+
+// Clusters of the latency form that fit on the device at once for this
+// shape (NTT forms, k + 1 <= 8), or 0.
+int cluster_capacity(const LaunchShape &S);
 
 // a1-a8: linear part, window shift, modulus switch, blind rotation (NTT form),
 // SampleExtract, +1/8.  ext: [count][k*N + 1].  If abar_out != nullptr the
@@ -131,12 +135,14 @@ MK_DECLARE_BOOTSTRAP(10, 2, 0)
 
 // Cluster (latency) form of the NTT blind rotation, one translation unit per
 // (ring dimension, field): mk_brc.cu built with -DMK_LOGN -DMK_FIELD.  Same
-// arguments as the launchers above; needs k + 1 <= 8.
+// arguments as the launchers above; needs k + 1 <= 8.  cluster_capacity_*:
+// the clusters of k + 1 CTAs that fit on the device at once (0: none).
 #define MK_DECLARE_CLUSTER(LOGN, F)                                                                            \
     cudaError_t launch_cluster_logn##LOGN##_f##F(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc, \
                                                  const uint32_t *ct_a, const uint32_t *ct_b,                    \
                                                  const uint32_t *abar_in, int64_t max_steps, uint32_t *ext,     \
-                                                 uint32_t *acc_out, uint32_t count, cudaStream_t st);
+                                                 uint32_t *acc_out, uint32_t count, cudaStream_t st);          \
+    int cluster_capacity_logn##LOGN##_f##F(uint32_t k, uint32_t n);
 MK_DECLARE_CLUSTER(8, 0)
 MK_DECLARE_CLUSTER(8, 1)
 MK_DECLARE_CLUSTER(10, 0)

@@ -388,6 +388,14 @@ BootstrapFn pick_cluster(const LaunchShape &S, uint32_t count) {
 }
 }  // namespace
 
+int cluster_capacity(const LaunchShape &S) {
+    if (S.k + 1 > 8 || (S.form != MK_FORM_NTT && S.form != MK_FORM_NTT2)) return 0;
+    if (S.logN == 8) return S.form == MK_FORM_NTT ? cluster_capacity_logn8_f0(S.k, S.n) : cluster_capacity_logn8_f1(S.k, S.n);
+    if (S.logN == 10)
+        return S.form == MK_FORM_NTT ? cluster_capacity_logn10_f0(S.k, S.n) : cluster_capacity_logn10_f1(S.k, S.n);
+    return 0;
+}
+
 cudaError_t launch_bootstrap_ntt(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                                  const uint32_t *ct_a, const uint32_t *ct_b, uint32_t *ext, uint32_t count,
                                  cudaStream_t st) {

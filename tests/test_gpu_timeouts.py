@@ -1,9 +1,10 @@
 """The kernels' bounded waits, run out on purpose without faulting anything.
 
-Two kernels wait on mbarriers for asynchronous copies: the staged blind
+Three kernels wait on mbarriers for asynchronous copies: the staged blind
 rotation (variant 6: each CMux step's key entry, bulk-copied into shared
-memory) and the tcgen05 product engine of the tensor form (digit tiles by
-TMA).  The test hook mk_debug_fault makes one such copy never be issued, so
+memory), the cluster latency form (each CTA's key polynomials of the step,
+bulk-copied) and the tcgen05 product engine of the tensor form (digit tiles
+by TMA).  The test hook mk_debug_fault makes one such copy never be issued, so
 the waits for it give up after a short bound; the kernel then lets its own
 copies and tensor-core operations finish, records the timeout and returns.
 Checked: mk_sync reports MK_ETIMEOUT (once), and the next ordinary gate call
@@ -60,6 +61,16 @@ def test_staged_kernel_key_copy_wait_runs_out(gpu_ready):
     ctx.set_form("ntt2")
     ctx.set_variant(6)
     ctx.set_cluster("off")
+    _timeout_then_recover(P, keys, ctx, g, c1, c2, "skip_key_step", 5)
+    ctx.close()
+
+
+def test_cluster_kernel_key_copy_wait_runs_out(gpu_ready):
+    """The cluster form keeps passing its cluster barriers after a wait runs
+    out (no CTA of a cluster may leave early), so only the status tells."""
+    P, keys, ctx, g, c1, c2 = _toy()
+    ctx.set_form("ntt2")
+    ctx.set_cluster("on")
     _timeout_then_recover(P, keys, ctx, g, c1, c2, "skip_key_step", 5)
     ctx.close()
 
