@@ -61,7 +61,7 @@ struct ClusterCtl {
 // destinations, 16-byte aligned), then the exchange buffer, the shares of v
 // (read in CTAs 0..ND-1), NTT(w_0..w_2) (read in CTAs 0 and i), ACC_jj, the
 // control block and the mod-switched words.  vbuf and wbuf hold thread tid's
-// element c at c * (N/8) + tid.
+// element c at c * T + tid (T threads per CTA).
 struct ClusterLayout {
     size_t keyA, keyD, keyF, xbuf, vbuf, wbuf, acc, ctl, abar, total;
 };
@@ -125,16 +125,16 @@ __device__ __forceinline__ void cl_issue(ClusterCtl *ctl, int b, uint32_t dst, c
     ctl->issued[b] += 1;
 }
 
-template <class F, int LOGN>
-__global__ void __launch_bounds__((1 << LOGN) / 8, 1)
+template <class F, int LOGN, int EPT>
+__global__ void __launch_bounds__((1 << LOGN) / EPT, 1)
 bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
                          const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
                          const uint32_t *__restrict__ abar_in, int64_t max_steps, uint32_t *__restrict__ ext,
                          uint32_t *__restrict__ acc_out) {
-    constexpr int N = 1 << LOGN, T = N / 8;
+    constexpr int N = 1 << LOGN, T = N / EPT;
     using E = typename F::E;
     using Tw = typename F::Tw;
-    using NT = Ntt<F, LOGN, true>;
+    using NT = Ntt<F, LOGN, true, EPT>;
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
@@ -190,7 +190,7 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     }
     const uint32_t bbar = abar[S.k * S.n];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < EPT; ++c) {
         const uint32_t m = tid + T * c;
         uint32_t r = m + bbar;
         if (r >= 2 * N) r -= 2 * N;
@@ -211,13 +211,13 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
         const int i = (int)(s / n) + 1;
         const bool with_f = (jj == 0 || jj == i);
         // 1. digits of (X^-e - 1) ACC_jj, one forward pass, c'_jj and v_jj
-        E C[8], V[8];
+        E C[EPT], V[EPT];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) C[c] = V[c] = F::zero();
+        for (int c = 0; c < EPT; ++c) C[c] = V[c] = F::zero();
         {
-            E x[3][8];
+            E x[3][EPT];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < EPT; ++c) {
                 const uint32_t m = tid + T * c;
                 uint32_t r = m + e;
                 if (r >= 2 * N) r -= 2 * N;
@@ -230,14 +230,14 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
             NT::template forward<3>(x, tid, twf, xbuf);
             cl_wait(barD, nD & 1u, ctl, S.wait_ns, K.status);
             ++nD;
-            mac_npf<F, LOGN, 8, 3, true>(C, x, keyD_s, tid);  // d_1..d_3
-            mac_npf<F, LOGN, 8, 3, true>(V, x, keyA_s, tid);  // -a or pk_jj
+            mac_npf<F, LOGN, EPT, 3, true>(C, x, keyD_s, tid);  // d_1..d_3
+            mac_npf<F, LOGN, EPT, 3, true>(V, x, keyA_s, tid);  // -a or pk_jj
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             if (r >= ND) break;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) vdst[r][(size_t)jj * N + c * T + tid] = V[c];
+            for (int c = 0; c < EPT; ++c) vdst[r][(size_t)jj * N + c * T + tid] = V[c];
         }
         __syncthreads();  // every read of this step's d is done
         if (tid == 0) {
@@ -249,24 +249,24 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
         if (jj < ND) {
             // 2. v = sum of the shares, w = g^-1(v), NTT of this CTA's digits of w to CTAs 0 and i
             E *wbuf_i = jj == i ? wbuf : cluster.map_shared_rank(wbuf, i);
-            E y[1][8];
+            E y[1][EPT];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) y[0][c] = vbuf[c * T + tid];
+            for (int c = 0; c < EPT; ++c) y[0][c] = vbuf[c * T + tid];
             for (int q = 1; q <= k; ++q)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) y[0][c] = fadd(y[0][c], vbuf[(size_t)q * N + c * T + tid]);
+                for (int c = 0; c < EPT; ++c) y[0][c] = fadd(y[0][c], vbuf[(size_t)q * N + c * T + tid]);
             NT::template inverse<1>(y, tid, twi, xbuf);
-            uint32_t vv[8];
+            uint32_t vv[EPT];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) vv[c] = F::to_u32(y[0][c]);
+            for (int c = 0; c < EPT; ++c) vv[c] = F::to_u32(y[0][c]);
 #pragma unroll 1
             for (int l = jj; l < 3; l += ND) {
-                E x[1][8];
+                E x[1][EPT];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) x[0][c] = F::from_digit(G.digit(vv[c], l));
+                for (int c = 0; c < EPT; ++c) x[0][c] = F::from_digit(G.digit(vv[c], l));
                 NT::template forward<1>(x, tid, twf, xbuf);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < EPT; ++c) {
                     wbuf0[(size_t)l * N + c * T + tid] = x[0][c];
                     wbuf_i[(size_t)l * N + c * T + tid] = x[0][c];
                 }
@@ -277,12 +277,12 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
             // 3a. c'_0 += <w, f0>, c'_i += <w, f1>
             cl_wait(barF, nF & 1u, ctl, S.wait_ns, K.status);
             ++nF;
-            E w[3][8];
+            E w[3][EPT];
 #pragma unroll
             for (int l = 0; l < 3; ++l)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) w[l][c] = wbuf[(size_t)l * N + c * T + tid];
-            mac_npf<F, LOGN, 8, 3, true>(C, w, keyF_s, tid);
+                for (int c = 0; c < EPT; ++c) w[l][c] = wbuf[(size_t)l * N + c * T + tid];
+            mac_npf<F, LOGN, EPT, 3, true>(C, w, keyF_s, tid);
             __syncthreads();  // every read of this step's f is done
             if (tid == 0) {
                 const int64_t sf = cl_next_step(abar, s + 1, limit, true, jj, n);
@@ -293,12 +293,12 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
         }
         // 3b. ACC_jj += c'_jj
         {
-            E y[1][8];
+            E y[1][EPT];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) y[0][c] = C[c];
+            for (int c = 0; c < EPT; ++c) y[0][c] = C[c];
             NT::template inverse<1>(y, tid, twi, xbuf);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[tid + T * c] += F::to_u32(y[0][c]);
+            for (int c = 0; c < EPT; ++c) acc[tid + T * c] += F::to_u32(y[0][c]);
         }
         __syncthreads();
     }
@@ -330,17 +330,23 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     cluster.sync();  // no CTA leaves while another could still address its shared memory
 }
 
+// Elements of a polynomial per thread in the cluster kernel (N / kClusterEpt
+// threads per CTA).  One CTA per SM runs here, so latency is hidden by warps
+// rather than by other CTAs: 4 (eight warps, two butterfly stages per
+// register pass) measured 10-12 % faster per gate than 8 on GB300.
+constexpr int kClusterEpt = 4;
+
 // Clusters of this shape that can be resident at once (one wave of gates), or
 // 0 if the device cannot run them.
 template <class F, int LOGN>
 int cluster_capacity(uint32_t k, uint32_t n) {
     if (k + 1 > 8) return 0;
     const ClusterLayout L = cluster_layout<F, LOGN>(k, n);
-    auto kern = bootstrap_cluster_kernel<F, LOGN>;
+    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(k + 1, 1, 1);
-    cfg.blockDim = dim3((1 << LOGN) / 8, 1, 1);
+    cfg.blockDim = dim3((1 << LOGN) / kClusterEpt, 1, 1);
     cfg.dynamicSmemBytes = L.total;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -362,12 +368,12 @@ cudaError_t launch_bootstrap_cluster(const LaunchShape &S, const DeviceKeys &K, 
     if (count == 0) return cudaSuccess;
     if (S.k + 1 > 8 || K.status == nullptr) return cudaErrorInvalidValue;
     const ClusterLayout L = cluster_layout<F, LOGN>(S.k, S.n);
-    auto kern = bootstrap_cluster_kernel<F, LOGN>;
+    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * (S.k + 1), 1, 1);
-    cfg.blockDim = dim3((1 << LOGN) / 8, 1, 1);
+    cfg.blockDim = dim3((1 << LOGN) / kClusterEpt, 1, 1);
     cfg.dynamicSmemBytes = L.total;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
