@@ -306,6 +306,37 @@ def test_toy_cluster_form_stages_bit_exact(toy, form):
         ctx.set_cluster("auto")
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_toy_cluster_form_party_counts(gpu_ready, k):
+    """The cluster form's digit split at the party counts the other tests do
+    not reach: k = 1 (two CTAs, CTA 0 transforms digits 0 and 2 of w) and
+    k = 3 (CTA 3 takes no digit).  Joint-key gates forced through the form,
+    word for word against the oracle and the batched kernel."""
+    import torch
+    from oracle import oracle as o
+    from paper_2205_05825_gb300 import workloads as W
+    P = W.toy_params(k)
+    keys = oracle_keys(P)
+    ctx = _ctx(P, keys)
+    G = 12
+    types, b1, b2 = W.random_gates(G, config_id=80 + k)
+    c1 = o.encrypt_joint(P, keys, b1, W.encryption_seed(80 + k, 0))
+    c2 = o.encrypt_joint(P, keys, b2, W.encryption_seed(80 + k, 1))
+    d = (to_dev(types.astype(np.uint8)), to_dev(c1), to_dev(c2))
+    outs = {}
+    for form in ("ntt2", "ntt"):
+        ctx.set_form(form)
+        for mode in ("on", "off"):
+            ctx.set_cluster(mode)
+            out = torch.zeros((G, ctx.W), dtype=torch.int32, device="cuda")
+            ctx.gates(*d, out)
+            outs[form, mode] = from_dev(out)
+    ref = o.gates(P, keys, types, c1, c2)
+    for v in outs.values():
+        assert np.array_equal(v, ref)
+    ctx.close()
+
+
 @pytest.mark.parametrize("k", [2, 4, 7])
 def test_full_cluster_form_sampled(gpu_ready, k):
     """Full size, cluster form forced on, joint-key inputs (all k*n steps):
