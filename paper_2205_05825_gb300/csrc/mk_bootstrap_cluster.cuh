@@ -63,13 +63,17 @@ struct ClusterCtl {
 // control block and the mod-switched words.  vbuf and wbuf hold thread tid's
 // element c at c * T + tid (T threads per CTA).
 struct ClusterLayout {
-    size_t keyA, keyD, keyF, xbuf, vbuf, wbuf, acc, ctl, abar, total;
+    size_t keyA, keyD, keyF, xbuf, vbuf, wbuf, acc, twf, twi, ctl, abar, total;
 };
 
-template <class F, int LOGN>
+// TWS: the forward and inverse twiddle tables copied into shared memory
+// (padded, one entry in 4) instead of read through L1.
+template <class F, int LOGN, bool TWS>
 __host__ __device__ inline ClusterLayout cluster_layout(uint32_t k, uint32_t n) {
     constexpr size_t N = (size_t)1 << LOGN;
     using E = typename F::E;
+    using Tw = typename F::Tw;
+    constexpr size_t tw_bytes = TWS ? ((sizeof(Tw) * (N + N / 4) + 15) & ~size_t(15)) : 0;
     ClusterLayout L;
     L.keyA = 0;
     L.keyD = L.keyA + sizeof(E) * 3 * N;
@@ -78,7 +82,9 @@ __host__ __device__ inline ClusterLayout cluster_layout(uint32_t k, uint32_t n) 
     L.vbuf = L.xbuf + sizeof(E) * 3 * padded_len(N);  // three padded polynomials per forward pass
     L.wbuf = L.vbuf + sizeof(E) * (k + 1) * N;
     L.acc = L.wbuf + sizeof(E) * 3 * N;
-    L.ctl = L.acc + sizeof(uint32_t) * N;
+    L.twf = L.acc + sizeof(uint32_t) * N;
+    L.twi = L.twf + tw_bytes;
+    L.ctl = L.twi + tw_bytes;
     L.abar = L.ctl + ((sizeof(ClusterCtl) + 15) & ~size_t(15));
     L.total = L.abar + ((sizeof(uint16_t) * (k * n + 1) + 15) & ~size_t(15));
     return L;
@@ -125,7 +131,7 @@ __device__ __forceinline__ void cl_issue(ClusterCtl *ctl, int b, uint32_t dst, c
     ctl->issued[b] += 1;
 }
 
-template <class F, int LOGN, int EPT>
+template <class F, int LOGN, int EPT, bool TWS>
 __global__ void __launch_bounds__((1 << LOGN) / EPT, 1)
 bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
                          const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
@@ -134,7 +140,7 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     constexpr int N = 1 << LOGN, T = N / EPT;
     using E = typename F::E;
     using Tw = typename F::Tw;
-    using NT = Ntt<F, LOGN, true, EPT>;
+    using NT = Ntt<F, LOGN, !TWS, EPT>;
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
     const int tid = threadIdx.x;
@@ -142,7 +148,7 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     const int jj = (int)cluster.block_rank();  // this CTA's accumulator polynomial
     const int ND = k + 1 < 3 ? k + 1 : 3;      // CTAs that transform the digits of w
     const uint32_t gate = blockIdx.x / (S.k + 1);
-    const ClusterLayout L = cluster_layout<F, LOGN>(S.k, S.n);
+    const ClusterLayout L = cluster_layout<F, LOGN, TWS>(S.k, S.n);
     const E *keyA_s = reinterpret_cast<const E *>(smem + L.keyA);
     const E *keyD_s = reinterpret_cast<const E *>(smem + L.keyD);
     const E *keyF_s = reinterpret_cast<const E *>(smem + L.keyF);
@@ -152,8 +158,16 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
     ClusterCtl *ctl = reinterpret_cast<ClusterCtl *>(smem + L.ctl);
     uint16_t *abar = reinterpret_cast<uint16_t *>(smem + L.abar);
-    const Tw *twf = static_cast<const Tw *>(K.tw_fwd);
-    const Tw *twi = static_cast<const Tw *>(K.tw_inv);
+    const Tw *twf, *twi;
+    if constexpr (TWS) {
+        twf = reinterpret_cast<const Tw *>(smem + L.twf);
+        twi = reinterpret_cast<const Tw *>(smem + L.twi);
+        load_twiddles<F, LOGN, EPT>(K, reinterpret_cast<Tw *>(smem + L.twf), reinterpret_cast<Tw *>(smem + L.twi),
+                                    tid);
+    } else {
+        twf = static_cast<const Tw *>(K.tw_fwd);
+        twi = static_cast<const Tw *>(K.tw_inv);
+    }
     const E *bk_all = static_cast<const E *>(K.bk);
     const E *keyA = static_cast<const E *>(K.keyA);
     const Gadget G = make_gadget(S.bg_bit);
@@ -335,29 +349,63 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
 // rather than by other CTAs: 4 (eight warps, two butterfly stages per
 // register pass) measured 10-12 % faster per gate than 8 on GB300.
 constexpr int kClusterEpt = 4;
+constexpr size_t kClusterSmemMax = 227 * 1024;
 
-// Clusters of this shape that can be resident at once (one wave of gates), or
-// 0 if the device cannot run them.
+// The twiddle tables go into shared memory where they fit beside the rest.
 template <class F, int LOGN>
-int cluster_capacity(uint32_t k, uint32_t n) {
-    if (k + 1 > 8) return 0;
-    const ClusterLayout L = cluster_layout<F, LOGN>(k, n);
-    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess) return 0;
+__host__ __device__ inline bool cluster_tws(uint32_t k, uint32_t n) {
+    return cluster_layout<F, LOGN, true>(k, n).total <= kClusterSmemMax;
+}
+
+template <class F, int LOGN, bool TWS>
+cudaLaunchConfig_t cluster_config(uint32_t k, uint32_t n, uint32_t count, cudaStream_t st, cudaLaunchAttribute *attr) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(k + 1, 1, 1);
+    cfg.gridDim = dim3(count * (k + 1), 1, 1);
     cfg.blockDim = dim3((1 << LOGN) / kClusterEpt, 1, 1);
-    cfg.dynamicSmemBytes = L.total;
-    cudaLaunchAttribute attr[1];
+    cfg.dynamicSmemBytes = cluster_layout<F, LOGN, TWS>(k, n).total;
+    cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = k + 1;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <class F, int LOGN, bool TWS>
+int cluster_capacity_t(uint32_t k, uint32_t n) {
+    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt, TWS>;
+    const size_t smem = cluster_layout<F, LOGN, TWS>(k, n).total;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = cluster_config<F, LOGN, TWS>(k, n, 1, nullptr, attr);
     int clusters = 0;
     if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) return 0;
     return clusters;
+}
+
+// Clusters of this shape that can be resident at once (one wave of gates), or
+// 0 if the device cannot run them.
+template <class F, int LOGN>
+int cluster_capacity(uint32_t k, uint32_t n) {
+    if (k + 1 > 8) return 0;
+    return cluster_tws<F, LOGN>(k, n) ? cluster_capacity_t<F, LOGN, true>(k, n)
+                                      : cluster_capacity_t<F, LOGN, false>(k, n);
+}
+
+template <class F, int LOGN, bool TWS>
+cudaError_t launch_bootstrap_cluster_t(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
+                                       const uint32_t *ct_a, const uint32_t *ct_b, const uint32_t *abar_in,
+                                       int64_t max_steps, uint32_t *ext, uint32_t *acc_out, uint32_t count,
+                                       cudaStream_t st) {
+    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt, TWS>;
+    const size_t smem = cluster_layout<F, LOGN, TWS>(S.k, S.n).total;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = cluster_config<F, LOGN, TWS>(S.k, S.n, count, st, attr);
+    return cudaLaunchKernelEx(&cfg, kern, S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);
 }
 
 template <class F, int LOGN>
@@ -367,23 +415,11 @@ cudaError_t launch_bootstrap_cluster(const LaunchShape &S, const DeviceKeys &K, 
                                      cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     if (S.k + 1 > 8 || K.status == nullptr) return cudaErrorInvalidValue;
-    const ClusterLayout L = cluster_layout<F, LOGN>(S.k, S.n);
-    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(count * (S.k + 1), 1, 1);
-    cfg.blockDim = dim3((1 << LOGN) / kClusterEpt, 1, 1);
-    cfg.dynamicSmemBytes = L.total;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = S.k + 1;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);
+    if (cluster_tws<F, LOGN>(S.k, S.n))
+        return launch_bootstrap_cluster_t<F, LOGN, true>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out,
+                                                         count, st);
+    return launch_bootstrap_cluster_t<F, LOGN, false>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out,
+                                                      count, st);
 }
 
 }  // namespace br
