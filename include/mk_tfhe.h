@@ -115,8 +115,8 @@ int mk_ctx_set_batch(mk_ctx *ctx, uint32_t max_gates_per_launch);
 
 /* Latency (cluster) form of the NTT blind rotation: one thread-block cluster
  * of k+1 CTAs per gate, CTA j owning accumulator polynomial j, so one gate
- * runs about k/2 times faster than in the batched kernel while the GPU has
- * SMs to spare.  MK_CLUSTER_AUTO (default) uses it for launches of at most
+ * runs two to four times faster than in the batched kernel (k = 2 to 7)
+ * while the GPU has SMs to spare.  MK_CLUSTER_AUTO (default) uses it for launches of at most
  * max(1, floor(k/2)) waves of gates, a wave being the clusters the device
  * can hold at once (queried when the keys are laid out for the form); _ON
  * for every launch, _OFF never.  Only the NTT forms with k <= 7; results are
