@@ -352,10 +352,10 @@ struct mk_ctx {
         // AUTO: the cluster kernel while the launch's gates fit in max(1,
         // floor(k/2)) waves of resident clusters (cluster_cap, queried from
         // the device for the form's kernel); beyond that the batched kernel's
-        // throughput wins.  One gate runs about k/2 times faster in the
-        // cluster form (GB300: 22.6 vs 31.3 ms at k = 2, 47.3 vs 99.0 at
-        // k = 4, 84.8 vs 306 at k = 7), and the measured crossovers sit at
-        // one, two and three waves.  Without a capacity: SM count / (k + 1).
+        // throughput wins.  One gate runs 2-4 times faster in the cluster
+        // form (GB300: 16.1 vs 31.3 ms at k = 2, 34.9 vs 99.0 at k = 4, 76.3
+        // vs 306 at k = 7), and the measured crossovers sit at one to two,
+        // two and three to four waves.  Without a capacity: SM count / (k + 1).
         const uint32_t waves = P.k >= 4 ? P.k / 2 : 1u;
         const uint32_t cmax = cluster_mode == MK_CLUSTER_ON    ? 0xFFFFFFFFu
                               : cluster_mode == MK_CLUSTER_OFF ? 0u
