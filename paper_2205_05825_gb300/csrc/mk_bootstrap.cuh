@@ -583,9 +583,14 @@ __device__ __forceinline__ void mac_npf(typename F::E (&A)[EPT], const typename 
 
 // One CMux step for party i (1..k) at rotation e:
 //   ACC += HP((X^{-e} - 1) ACC, BK_{i,j}).
-// Slots q = 0..k are the accumulator polynomials in the order 0, i, others
-// (phase A); slot k+1 is phase B (w = g^-1(v) against f0, f1).  NPF digit
-// polynomials go through one forward transform together.
+// Slots q = 0..k take the accumulator polynomials in the order: the k - 1
+// others (ascending, i left out), then 0, then i (phase A); slot k + 1 is
+// phase B (w = g^-1(v) against f0, f1).  NPF digit polynomials go through
+// one forward transform together.  The order lets every inverse transform
+// run in a pair (two polynomials per pass, twice the independent work of a
+// single): the others' c'_jj two by two, an odd last one with v, and c'_0
+// with c'_i.  Four accumulator sets: C0 and CI hold the first and second of
+// an others' pair, then c'_0 and c'_i; CJ the odd last other; V.
 template <class F, int LOGN, int NPF, bool TWG, int EPT>
 __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys &K, const Gadget &G,
                                           const typename F::E *bk, int i, uint32_t e, uint32_t *acc,
@@ -595,6 +600,8 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
     using E = typename F::E;
     constexpr int N = NT::N, T = NT::T;
     const int k = (int)S.k;
+    const int nothers = k - 1;
+    const int npaired = nothers & ~1;  // others that go through paired inverses
     const E *keyA = static_cast<const E *>(K.keyA);
     E C0[EPT], CI[EPT], CJ[EPT], V[EPT];
     uint32_t vv[EPT];
@@ -602,10 +609,13 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
     for (int c = 0; c < EPT; ++c) C0[c] = CI[c] = CJ[c] = V[c] = F::zero();
 #pragma unroll 1
     for (int q = 0; q <= k + 1; ++q) {
-        const int jj = (q == 0) ? 0 : (q == 1 ? i : (q - 1 < i ? q - 1 : q));  // q <= k only
-        if (q >= 2 && q <= k) {
+        // polynomial of slot q (q <= k): the q-th other (i skipped), 0, then i
+        const int jj = q < nothers ? (q + 1 < i ? q + 1 : q + 2) : (q == nothers ? 0 : i);
+        // accumulator of slot q: 0 = C0, 1 = CI, 2 = CJ
+        const int slot = q < npaired ? (q & 1) : (q < nothers ? 2 : (q == nothers ? 0 : 1));
+        if (q <= k && slot < 2 && (q == nothers || (q < npaired && (q & 1) == 0))) {
 #pragma unroll
-            for (int c = 0; c < EPT; ++c) CJ[c] = F::zero();
+            for (int c = 0; c < EPT; ++c) C0[c] = CI[c] = F::zero();  // a fresh pair (or c'_0, c'_i)
         }
 #pragma unroll 1
         for (int l0 = 0; l0 < 3; l0 += NPF) {
@@ -633,8 +643,8 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
             if (q <= k) {
                 const E *kd = bk + l0 * N;                              // d_l0.. of BK_{i,j}
                 const E *ka = keyA + ((size_t)jj * 3 + l0) * N;         // -a_l0.. or pk_jj[l0..]
-                if (q == 0) mac_npf<F, LOGN, EPT, NPF>(C0, x, kd, tid);
-                else if (q == 1) mac_npf<F, LOGN, EPT, NPF>(CI, x, kd, tid);
+                if (slot == 0) mac_npf<F, LOGN, EPT, NPF>(C0, x, kd, tid);
+                else if (slot == 1) mac_npf<F, LOGN, EPT, NPF>(CI, x, kd, tid);
                 else mac_npf<F, LOGN, EPT, NPF>(CJ, x, kd, tid);
                 mac_npf<F, LOGN, EPT, NPF>(V, x, ka, tid);
             } else {
@@ -643,45 +653,41 @@ __device__ __forceinline__ void cmux_step(const LaunchShape &S, const DeviceKeys
             }
         }
         // Inverse transforms due after this slot (two call sites):
-        //   2 <= q < k:  c'_jj alone                      -> ACC_jj
-        //   q == k:      c'_jj (k >= 2) and v together    -> ACC_jj, v in registers
-        //   q == k + 1:  c'_0 and c'_i together           -> ACC_0, ACC_i
-        const bool pair = (q == k && k >= 2) || q == k + 1;
-        const bool single = (q >= 2 && q < k) || (q == k && k == 1);
-        if (pair) {
-            const bool last = (q == k + 1);
+        //   q < npaired, q odd:  the others' pair in C0, CI   -> ACC of both
+        //   q == k, odd others:  c'_last (CJ) and v together  -> ACC_last, v in registers
+        //   q == k, even others: v alone                      -> v in registers
+        //   q == k + 1:          c'_0 and c'_i together       -> ACC_0, ACC_i
+        const bool pair_others = q < npaired && (q & 1);
+        const bool pair_v = q == k && (nothers & 1);
+        const bool pair_last = q == k + 1;
+        if (pair_others || pair_v || pair_last) {
             E y[2][EPT];
 #pragma unroll
             for (int c = 0; c < EPT; ++c) {
-                y[0][c] = last ? C0[c] : CJ[c];
-                y[1][c] = last ? CI[c] : V[c];
+                y[0][c] = pair_v ? CJ[c] : C0[c];
+                y[1][c] = pair_v ? V[c] : CI[c];
             }
             NT::template inverse<2>(y, tid, twi, xbuf);
-            uint32_t *d0 = acc + (last ? 0 : jj) * N;
+            // destinations: the pair's polynomials (the previous other, this one), (last other, v), (0, i)
+            const int d0 = pair_others ? (jj - 1 == i ? jj - 2 : jj - 1) : (pair_v ? (nothers + 1 > i ? nothers + 1 : nothers) : 0);
+            uint32_t *p0 = acc + d0 * N;
 #pragma unroll
-            for (int c = 0; c < EPT; ++c) d0[tid + T * c] += F::to_u32(y[0][c]);
-            if (last) {
-                uint32_t *d1 = acc + i * N;
-#pragma unroll
-                for (int c = 0; c < EPT; ++c) d1[tid + T * c] += F::to_u32(y[1][c]);
-            } else {
+            for (int c = 0; c < EPT; ++c) p0[tid + T * c] += F::to_u32(y[0][c]);
+            if (pair_v) {
 #pragma unroll
                 for (int c = 0; c < EPT; ++c) vv[c] = F::to_u32(y[1][c]);
+            } else {
+                uint32_t *p1 = acc + (pair_others ? jj : i) * N;
+#pragma unroll
+                for (int c = 0; c < EPT; ++c) p1[tid + T * c] += F::to_u32(y[1][c]);
             }
-        } else if (single) {
-            const bool is_v = (q == k);
+        } else if (q == k) {
             E y[1][EPT];
 #pragma unroll
-            for (int c = 0; c < EPT; ++c) y[0][c] = is_v ? V[c] : CJ[c];
+            for (int c = 0; c < EPT; ++c) y[0][c] = V[c];
             NT::template inverse<1>(y, tid, twi, xbuf);
-            if (is_v) {
 #pragma unroll
-                for (int c = 0; c < EPT; ++c) vv[c] = F::to_u32(y[0][c]);
-            } else {
-                uint32_t *dst = acc + jj * N;
-#pragma unroll
-                for (int c = 0; c < EPT; ++c) dst[tid + T * c] += F::to_u32(y[0][c]);
-            }
+            for (int c = 0; c < EPT; ++c) vv[c] = F::to_u32(y[0][c]);
         }
     }
 }
