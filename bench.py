@@ -20,10 +20,14 @@ p50/p99, the one-gate-per-launch rate and the blind rotation's roofline) and
 bounded summaries of the other configurations -- the precision sweep
 (512 joint-key gates per party count and product form), the regression
 application (shallow netlists), the k-bit operators (8-bit throughput,
-16-bit single-pair latency, both netlist families) and the serving loop
+16-bit single-pair latency, both netlist families), Table 2's gates (each
+gate directly and composed of bootstrapped NANDs) and the serving loop
 (k = 4, 16-bit requests, a closed batch and Poisson arrivals at 0.5 and 0.9
-of its capacity, with the array and the shallow netlists).  --sweep, --regression and --operators run the full
-versions; --no-extras leaves the summaries out.
+of its capacity, with the array and the shallow netlists).  --sweep,
+--regression and --operators run the full versions; --no-extras leaves the
+summaries out.  The end-to-end figure ("e2e") times the same K steps through
+the public API with the inputs copied from pinned host memory and the
+outputs read back inside the timed region.
 """
 import argparse
 import hashlib
