@@ -32,6 +32,9 @@
 // copy is issued after it, but the CTA keeps passing every cluster barrier
 // (its results are then garbage; mk_sync reports MK_ETIMEOUT); before it
 // exits, thread 0 waits (bounded) for the last copy issued into each buffer.
+// The twiddle tables go into shared memory too where they fit (k <= 5 at
+// N = 1024); beyond that the public keys are read through L1 instead to make
+// room for them (k = 6, 7), and where even that does not fit, the twiddles.
 // Results are bit-identical to the batched kernel (the same exact field
 // arithmetic; sums mod p are order-independent).
 #pragma once
@@ -67,8 +70,9 @@ struct ClusterLayout {
 };
 
 // TWS: the forward and inverse twiddle tables copied into shared memory
-// (padded, one entry in 4) instead of read through L1.
-template <class F, int LOGN, bool TWS>
+// (padded, one entry in 4) instead of read through L1.  KAS: the CTA's public
+// keys staged in shared memory instead of read through L1.
+template <class F, int LOGN, bool TWS, bool KAS>
 __host__ __device__ inline ClusterLayout cluster_layout(uint32_t k, uint32_t n) {
     constexpr size_t N = (size_t)1 << LOGN;
     using E = typename F::E;
@@ -76,7 +80,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(uint32_t k, uint32_t n) 
     constexpr size_t tw_bytes = TWS ? ((sizeof(Tw) * (N + N / 4) + 15) & ~size_t(15)) : 0;
     ClusterLayout L;
     L.keyA = 0;
-    L.keyD = L.keyA + sizeof(E) * 3 * N;
+    L.keyD = L.keyA + (KAS ? sizeof(E) * 3 * N : 0);
     L.keyF = L.keyD + sizeof(E) * 3 * N;
     L.xbuf = L.keyF + sizeof(E) * 3 * N;
     L.vbuf = L.xbuf + sizeof(E) * 3 * padded_len(N);  // three padded polynomials per forward pass
@@ -131,7 +135,7 @@ __device__ __forceinline__ void cl_issue(ClusterCtl *ctl, int b, uint32_t dst, c
     ctl->issued[b] += 1;
 }
 
-template <class F, int LOGN, int EPT, bool TWS>
+template <class F, int LOGN, int EPT, bool TWS, bool KAS>
 __global__ void __launch_bounds__((1 << LOGN) / EPT, 1)
 bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict__ desc,
                          const uint32_t *__restrict__ ct_a, const uint32_t *__restrict__ ct_b,
@@ -148,7 +152,7 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     const int jj = (int)cluster.block_rank();  // this CTA's accumulator polynomial
     const int ND = k + 1 < 3 ? k + 1 : 3;      // CTAs that transform the digits of w
     const uint32_t gate = blockIdx.x / (S.k + 1);
-    const ClusterLayout L = cluster_layout<F, LOGN, TWS>(S.k, S.n);
+    const ClusterLayout L = cluster_layout<F, LOGN, TWS, KAS>(S.k, S.n);
     const E *keyA_s = reinterpret_cast<const E *>(smem + L.keyA);
     const E *keyD_s = reinterpret_cast<const E *>(smem + L.keyD);
     const E *keyF_s = reinterpret_cast<const E *>(smem + L.keyF);
@@ -194,7 +198,7 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     }
     __syncthreads();
     if (tid == 0) {  // A_jj once; d and f of the first active steps
-        cl_issue(ctl, 0, st_smem_addr(keyA_s), keyA + (size_t)jj * 3 * N, key_bytes, -1, -1);
+        if (KAS) cl_issue(ctl, 0, st_smem_addr(keyA_s), keyA + (size_t)jj * 3 * N, key_bytes, -1, -1);
         const int64_t sd = cl_next_step(abar, 0, limit, false, jj, n);
         if (sd < limit) cl_issue(ctl, 1, st_smem_addr(keyD_s), bk_all + (size_t)sd * 9 * N, key_bytes, sd, S.skip_key_step);
         const int64_t sf = cl_next_step(abar, 0, limit, true, jj, n);
@@ -215,7 +219,7 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
     for (int r = 0; r < 3; ++r) vdst[r] = (r < ND) ? (r == jj ? vbuf : cluster.map_shared_rank(vbuf, r)) : nullptr;
     E *wbuf0 = jj == 0 ? wbuf : cluster.map_shared_rank(wbuf, 0);
     cluster.sync();  // every CTA of the cluster is running before remote accesses
-    cl_wait(barA, 0, ctl, S.wait_ns, K.status);
+    if (KAS) cl_wait(barA, 0, ctl, S.wait_ns, K.status);
 
     uint32_t nD = 0, nF = 0;  // waits done on the D and F buffers
 #pragma unroll 1
@@ -245,7 +249,8 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
             cl_wait(barD, nD & 1u, ctl, S.wait_ns, K.status);
             ++nD;
             mac_npf<F, LOGN, EPT, 3, true>(C, x, keyD_s, tid);  // d_1..d_3
-            mac_npf<F, LOGN, EPT, 3, true>(V, x, keyA_s, tid);  // -a or pk_jj
+            if constexpr (KAS) mac_npf<F, LOGN, EPT, 3, true>(V, x, keyA_s, tid);  // -a or pk_jj
+            else mac_npf<F, LOGN, EPT, 3, false>(V, x, keyA + (size_t)jj * 3 * N, tid);
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -351,18 +356,23 @@ bootstrap_cluster_kernel(LaunchShape S, DeviceKeys K, const GateDesc *__restrict
 constexpr int kClusterEpt = 4;
 constexpr size_t kClusterSmemMax = 227 * 1024;
 
-// The twiddle tables go into shared memory where they fit beside the rest.
+// What goes into shared memory besides the step's keys, by fit: the twiddle
+// tables and the public keys (0), the twiddle tables only (1: large k), the
+// public keys only (2); -1 if not even the step's keys fit (large k n).
 template <class F, int LOGN>
-__host__ __device__ inline bool cluster_tws(uint32_t k, uint32_t n) {
-    return cluster_layout<F, LOGN, true>(k, n).total <= kClusterSmemMax;
+__host__ __device__ inline int cluster_mode(uint32_t k, uint32_t n) {
+    if (cluster_layout<F, LOGN, true, true>(k, n).total <= kClusterSmemMax) return 0;
+    if (cluster_layout<F, LOGN, true, false>(k, n).total <= kClusterSmemMax) return 1;
+    if (cluster_layout<F, LOGN, false, true>(k, n).total <= kClusterSmemMax) return 2;
+    return -1;
 }
 
-template <class F, int LOGN, bool TWS>
+template <class F, int LOGN, bool TWS, bool KAS>
 cudaLaunchConfig_t cluster_config(uint32_t k, uint32_t n, uint32_t count, cudaStream_t st, cudaLaunchAttribute *attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(count * (k + 1), 1, 1);
     cfg.blockDim = dim3((1 << LOGN) / kClusterEpt, 1, 1);
-    cfg.dynamicSmemBytes = cluster_layout<F, LOGN, TWS>(k, n).total;
+    cfg.dynamicSmemBytes = cluster_layout<F, LOGN, TWS, KAS>(k, n).total;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = k + 1;
@@ -373,13 +383,13 @@ cudaLaunchConfig_t cluster_config(uint32_t k, uint32_t n, uint32_t count, cudaSt
     return cfg;
 }
 
-template <class F, int LOGN, bool TWS>
+template <class F, int LOGN, bool TWS, bool KAS>
 int cluster_capacity_t(uint32_t k, uint32_t n) {
-    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt, TWS>;
-    const size_t smem = cluster_layout<F, LOGN, TWS>(k, n).total;
+    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt, TWS, KAS>;
+    const size_t smem = cluster_layout<F, LOGN, TWS, KAS>(k, n).total;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = cluster_config<F, LOGN, TWS>(k, n, 1, nullptr, attr);
+    const cudaLaunchConfig_t cfg = cluster_config<F, LOGN, TWS, KAS>(k, n, 1, nullptr, attr);
     int clusters = 0;
     if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) return 0;
     return clusters;
@@ -390,21 +400,25 @@ int cluster_capacity_t(uint32_t k, uint32_t n) {
 template <class F, int LOGN>
 int cluster_capacity(uint32_t k, uint32_t n) {
     if (k + 1 > 8) return 0;
-    return cluster_tws<F, LOGN>(k, n) ? cluster_capacity_t<F, LOGN, true>(k, n)
-                                      : cluster_capacity_t<F, LOGN, false>(k, n);
+    switch (cluster_mode<F, LOGN>(k, n)) {
+        case 0: return cluster_capacity_t<F, LOGN, true, true>(k, n);
+        case 1: return cluster_capacity_t<F, LOGN, true, false>(k, n);
+        case 2: return cluster_capacity_t<F, LOGN, false, true>(k, n);
+        default: return 0;
+    }
 }
 
-template <class F, int LOGN, bool TWS>
+template <class F, int LOGN, bool TWS, bool KAS>
 cudaError_t launch_bootstrap_cluster_t(const LaunchShape &S, const DeviceKeys &K, const GateDesc *desc,
                                        const uint32_t *ct_a, const uint32_t *ct_b, const uint32_t *abar_in,
                                        int64_t max_steps, uint32_t *ext, uint32_t *acc_out, uint32_t count,
                                        cudaStream_t st) {
-    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt, TWS>;
-    const size_t smem = cluster_layout<F, LOGN, TWS>(S.k, S.n).total;
+    auto kern = bootstrap_cluster_kernel<F, LOGN, kClusterEpt, TWS, KAS>;
+    const size_t smem = cluster_layout<F, LOGN, TWS, KAS>(S.k, S.n).total;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = cluster_config<F, LOGN, TWS>(S.k, S.n, count, st, attr);
+    const cudaLaunchConfig_t cfg = cluster_config<F, LOGN, TWS, KAS>(S.k, S.n, count, st, attr);
     return cudaLaunchKernelEx(&cfg, kern, S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out);
 }
 
@@ -415,11 +429,19 @@ cudaError_t launch_bootstrap_cluster(const LaunchShape &S, const DeviceKeys &K, 
                                      cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     if (S.k + 1 > 8 || K.status == nullptr) return cudaErrorInvalidValue;
-    if (cluster_tws<F, LOGN>(S.k, S.n))
-        return launch_bootstrap_cluster_t<F, LOGN, true>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out,
-                                                         count, st);
-    return launch_bootstrap_cluster_t<F, LOGN, false>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext, acc_out,
-                                                      count, st);
+    switch (cluster_mode<F, LOGN>(S.k, S.n)) {
+        case 0:
+            return launch_bootstrap_cluster_t<F, LOGN, true, true>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
+                                                                   acc_out, count, st);
+        case 1:
+            return launch_bootstrap_cluster_t<F, LOGN, true, false>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
+                                                                    acc_out, count, st);
+        case 2:
+            return launch_bootstrap_cluster_t<F, LOGN, false, true>(S, K, desc, ct_a, ct_b, abar_in, max_steps, ext,
+                                                                    acc_out, count, st);
+        default:
+            return cudaErrorInvalidConfiguration;  // the shape needs more shared memory than a CTA has
+    }
 }
 
 }  // namespace br

@@ -337,7 +337,7 @@ struct mk_ctx {
     int circuit_exec = MK_EXEC_AUTO;      // operators: one launch pair per level, or one persistent launch
     int64_t debug_skip_item = -1;         // test hook of the persistent launch (mk_debug_fault)
     uint32_t sm_count = 0;
-    uint32_t cluster_cap = 0;  // resident clusters of the latency form (for the keys' form; 0: unknown)
+    uint32_t cluster_cap = 0;  // resident clusters of the latency form for the keys' form (0: none)
     cudaStream_t capture_stream = nullptr;  // non-default stream the graphs are captured on
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[2];
     std::vector<cudaEvent_t> ev_pool;
@@ -355,12 +355,12 @@ struct mk_ctx {
         // throughput wins.  One gate runs 2-4 times faster in the cluster
         // form (GB300: 16.1 vs 31.3 ms at k = 2, 34.9 vs 99.0 at k = 4, 76.3
         // vs 306 at k = 7), and the measured crossovers sit at one to two,
-        // two and three to four waves.  Without a capacity: SM count / (k + 1).
+        // two and three to four waves.  A capacity of 0 (other forms, k > 7,
+        // or a shape whose CTA does not fit in shared memory) keeps it off.
         const uint32_t waves = P.k >= 4 ? P.k / 2 : 1u;
         const uint32_t cmax = cluster_mode == MK_CLUSTER_ON    ? 0xFFFFFFFFu
                               : cluster_mode == MK_CLUSTER_OFF ? 0u
-                              : cluster_cap                    ? waves * cluster_cap
-                                                               : sm_count / (P.k + 1);
+                                                               : waves * cluster_cap;
         return LaunchShape{P.n, P.N, logN, P.k, P.d, P.bg_bit, P.ks_bit, P.t, variant, form, cmax, wait_ns,
                            debug_skip_key_step};
     }

@@ -46,8 +46,10 @@ class Bar:
         return (self.completed & 1) != parity
 
 
-def run_cta(k, n, jj, abar, limit, rng, skip=-1, bound=60, mutant=None):
-    """The kernel's sequence for CTA jj; returns (timed_out, log)."""
+def run_cta(k, n, jj, abar, limit, rng, skip=-1, bound=60, mutant=None, stage_a=True):
+    """The kernel's sequence for CTA jj; returns (timed_out, log).  stage_a:
+    the public keys are staged (the layouts where they fit); otherwise they
+    are read through L1 and the A buffer is never used."""
     now = [0]
     bars = {b: Bar() for b in "ADF"}
     abort = [False]
@@ -91,14 +93,15 @@ def run_cta(k, n, jj, abar, limit, rng, skip=-1, bound=60, mutant=None):
                 return False
             tick()
 
-    issue("A", -1)
+    if stage_a:
+        issue("A", -1)
     s = next_step(0, False)
     if s < limit:
         issue("D", s)
     s = next_step(0, True)
     if s < limit:
         issue("F", s)
-    if wait("A", 0):
+    if stage_a and wait("A", 0):
         assert bars["A"].content == -1
     nd = nf = 0
     for s in range(limit):
@@ -144,15 +147,16 @@ def _abar(k, n, rng, zeros=0.15):
     return [0 if rng.random() < zeros else rng.randint(1, 511) for _ in range(k * n)]
 
 
+@pytest.mark.parametrize("stage_a", [True, False])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 7])
-def test_every_wait_sees_its_step(k):
+def test_every_wait_sees_its_step(k, stage_a):
     rng = random.Random(100 + k)
     n = 13
     for trial in range(40):
         abar = _abar(k, n, rng, zeros=rng.choice([0.0, 0.2, 0.6]))
         limit = rng.choice([k * n, k * n, rng.randint(0, k * n)])
         for jj in range(k + 1):
-            timed_out, log = run_cta(k, n, jj, abar, limit, rng)
+            timed_out, log = run_cta(k, n, jj, abar, limit, rng, stage_a=stage_a)
             assert not timed_out
             d_steps = [s for (ev, b, *rest) in [(e[0], e[1], *e[2:]) for e in log] if ev == "issue" and b == "D"
                        for s in rest]
