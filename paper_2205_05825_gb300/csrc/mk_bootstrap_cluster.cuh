@@ -63,7 +63,7 @@ struct ClusterCtl {
 // Shared memory of one CTA: the staged key buffers first (bulk-copy
 // destinations, 16-byte aligned), then the exchange buffer, the shares of v
 // (read in CTAs 0..ND-1), NTT(w_0..w_2) (read in CTAs 0 and i), ACC_jj, the
-// control block and the mod-switched words.  vbuf and wbuf hold thread tid's
+// twiddle tables (when staged), the control block and the mod-switched words.  vbuf and wbuf hold thread tid's
 // element c at c * T + tid (T threads per CTA).
 struct ClusterLayout {
     size_t keyA, keyD, keyF, xbuf, vbuf, wbuf, acc, twf, twi, ctl, abar, total;
